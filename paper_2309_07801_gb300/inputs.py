@@ -1,0 +1,169 @@
+"""Seeded synthetic inputs for the colour-gradient D3Q27 step.
+
+This module holds no arithmetic of the method itself: it only draws initial
+fields (per-colour densities, velocity, solid mask) and parameter sets shaped
+like the paper's test problems.  The same arrays feed the CUDA path and the
+CPU oracle, so both see identical inputs.
+
+Recipe (the paper is silent on initial profiles; Sec. IV gives the setups):
+  * interface profile  phi0(r) = tanh(2 (R - r) / W), W = 4 cells;
+  * rho_r = rho_r0 (1 + phi0) / 2,  rho_b = rho_b0 (1 - phi0) / 2,
+    which the order parameter of Sec. II.A maps back to phi0 exactly;
+  * optional noise from a splitmix64 stream (top 53 bits -> [0, 1)).
+Rest fractions follow the pressure balance of Sec. II.A: the lighter phase
+takes alpha = 8/27 (c_s^2 = 1/3, as in the bubble test of Sec. IV.D), the
+heavier one 1 - alpha = (1 - 8/27) / ratio.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, asdict
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+_MASK64 = (1 << 64) - 1
+
+
+def splitmix64(seed: int, n: int) -> np.ndarray:
+    """n uniform doubles in [0, 1) from the splitmix64 generator (Steele et al.)."""
+    out = np.empty(n, dtype=np.float64)
+    # vectorised: state_k = seed + (k+1) * golden
+    k = np.arange(1, n + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (np.uint64(seed & _MASK64) + k * np.uint64(0x9E3779B97F4A7C15))
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    out[:] = (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    return out
+
+
+def rest_fractions(rho_r0: float, rho_b0: float) -> Tuple[float, float]:
+    """(alpha_r, alpha_b) for a density ratio: lighter phase 8/27."""
+    light = 8.0 / 27.0
+    gamma = rho_r0 / rho_b0
+    if gamma >= 1.0:
+        return 1.0 - (1.0 - light) / gamma, light
+    return light, 1.0 - (1.0 - light) * gamma
+
+
+@dataclass
+class Workload:
+    """Parameters of one domain in lattice units (mirrors the C struct)."""
+    nx: int
+    ny: int
+    nz: int
+    bc: Tuple[int, int, int] = (0, 0, 0)
+    rho_r0: float = 1.0
+    rho_b0: float = 1.0
+    alpha_r: float = 8.0 / 27.0
+    alpha_b: float = 8.0 / 27.0
+    nu_r: float = 0.1
+    nu_b: float = 0.1
+    sigma: float = 0.01
+    beta: float = 0.7
+    omega: Tuple[float, ...] = (1.0,) * 11
+    g: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    rho_ref: float = 0.0
+    force_mode: int = 0
+    model: int = 3
+    use_Q: int = 1
+    steps: int = 200
+    name: str = ""
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def params(self) -> dict:
+        d = asdict(self)
+        d.pop("steps"); d.pop("name")
+        return d
+
+
+def droplet_fields(shape_zyx, center_xyz, radius, rho_r0, rho_b0, width=4.0,
+                   u0=(0.0, 0.0, 0.0), semi_axes=None, noise=0.0, seed=0,
+                   invert=False):
+    """(rho_r, rho_b, u) for a red droplet (or blue bubble if invert) in a
+    periodic box; arrays are [nz, ny, nx] and u is [3, nz, ny, nx]."""
+    nz, ny, nx = shape_zyx
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    cx, cy, cz = center_xyz
+    if semi_axes is None:
+        r = np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2)
+        dist = radius - r
+    else:
+        ax, ay, az = semi_axes
+        q = np.sqrt(((x - cx) / ax) ** 2 + ((y - cy) / ay) ** 2 + ((z - cz) / az) ** 2)
+        dist = (1.0 - q) * min(ax, ay, az)
+    phi0 = np.tanh(2.0 * dist / width)
+    if invert:
+        phi0 = -phi0
+    rho_r = rho_r0 * (1.0 + phi0) / 2.0
+    rho_b = rho_b0 * (1.0 - phi0) / 2.0
+    u = np.empty((3, nz, ny, nx))
+    for a in range(3):
+        u[a] = u0[a]
+    if noise > 0.0:
+        n = nx * ny * nz
+        rnd = splitmix64(seed, 5 * n).reshape(5, nz, ny, nx) * 2.0 - 1.0
+        rho_r = rho_r * (1.0 + noise * rnd[0])
+        rho_b = rho_b * (1.0 + noise * rnd[1])
+        u = u + noise * rnd[2:5]
+    return rho_r, rho_b, u
+
+
+def layered_fields(nz, a, rho_r0, rho_b0, width=4.0):
+    """Layered channel: red in |z - zc| <= a, blue outside; walls at z=0, nz-1.
+    Returns fields of shape [nz, 1, 1]."""
+    zc = (nz - 1) / 2.0
+    z = np.arange(nz, dtype=np.float64)
+    phi0 = np.tanh(2.0 * (a - np.abs(z - zc)) / width)
+    rho_r = (rho_r0 * (1.0 + phi0) / 2.0).reshape(nz, 1, 1)
+    rho_b = (rho_b0 * (1.0 - phi0) / 2.0).reshape(nz, 1, 1)
+    u = np.zeros((3, nz, 1, 1))
+    return rho_r, rho_b, u
+
+
+# ---- the paper-shaped workloads (sizes, densities, viscosities) ---------------
+
+def static_droplet_32() -> Workload:
+    """32^3 periodic, R=8 centred, equal densities, nu=0.1, sigma=0.01."""
+    return Workload(32, 32, 32, nu_r=0.1, nu_b=0.1, sigma=0.01, beta=0.7,
+                    steps=200, name="static_droplet_32")
+
+
+def translating_droplet(edge=128) -> Workload:
+    """edge^3 periodic, ratio 10 (1 : 0.1), nu=0.05, sigma=0.005, u0=(0.05,0.05,0)."""
+    ar, ab = rest_fractions(1.0, 0.1)
+    return Workload(edge, edge, edge, rho_r0=1.0, rho_b0=0.1, alpha_r=ar, alpha_b=ab,
+                    nu_r=0.05, nu_b=0.05, sigma=0.005, beta=0.7, steps=4000,
+                    name="translating_droplet_%d" % edge)
+
+
+def rising_bubble(nx=192, ny=192, nz=384) -> Workload:
+    """Ratio 1000 bubble with z walls (liquid red rho=1, gas blue rho=0.001)."""
+    ar, ab = rest_fractions(1.0, 0.001)
+    return Workload(nx, ny, nz, bc=(0, 0, 1), rho_r0=1.0, rho_b0=0.001,
+                    alpha_r=ar, alpha_b=ab, nu_r=0.005, nu_b=0.05, sigma=0.01,
+                    beta=0.2, g=(0.0, 0.0, -1e-6), rho_ref=1.0, force_mode=3,
+                    steps=20000, name="rising_bubble_%dx%dx%d" % (nx, ny, nz))
+
+
+def workload_fields(wl: Workload, seed: int = 0, noise: float = 0.0):
+    """Initial fields for a named workload (droplet/bubble placement)."""
+    shape = (wl.nz, wl.ny, wl.nx)
+    if wl.name.startswith("static_droplet"):
+        c = (wl.nx / 2.0, wl.ny / 2.0, wl.nz / 2.0)
+        return droplet_fields(shape, c, wl.nx / 4.0, wl.rho_r0, wl.rho_b0,
+                              noise=noise, seed=seed)
+    if wl.name.startswith("translating_droplet"):
+        c = (wl.nx / 2.0, wl.ny / 2.0, wl.nz / 2.0)
+        return droplet_fields(shape, c, 20.0 * wl.nx / 128.0, wl.rho_r0, wl.rho_b0,
+                              u0=(0.05, 0.05, 0.0), noise=noise, seed=seed)
+    if wl.name.startswith("rising_bubble"):
+        c = (wl.nx / 2.0, wl.ny / 2.0, wl.nz / 6.0)
+        return droplet_fields(shape, c, wl.nx / 8.0, wl.rho_r0, wl.rho_b0,
+                              noise=noise, seed=seed, invert=True)
+    raise ValueError("unknown workload " + wl.name)

@@ -1,0 +1,184 @@
+"""Whole-domain pins of the FP64 oracle: conservation laws, symmetries, fixed
+points and closed-form flows that the method must reproduce."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2309_07801_gb300 import inputs
+
+
+def _droplet_domain(orc, n=16, ratio=10.0, noise=1e-3, bc=(0, 0, 0), **kw):
+    rr0, rb0 = 1.0, 1.0 / ratio
+    ar, ab = inputs.rest_fractions(rr0, rb0)
+    P = orc.make_params(n, n + 1, n + 2, bc=bc, rho_r0=rr0, rho_b0=rb0, alpha_r=ar,
+                        alpha_b=ab, nu_r=0.05, nu_b=0.08, sigma=0.01, beta=0.7, **kw)
+    d = orc.Domain(P)
+    rr, rb, u = inputs.droplet_fields((n + 2, n + 1, n), (n / 2, n / 2, n / 2), n / 4,
+                                      rr0, rb0, u0=(0.02, -0.01, 0.03), noise=noise, seed=3)
+    d.init(rr, rb, u)
+    return d
+
+
+def test_per_colour_mass_conserved_periodic(orc):
+    """P4: each colour's mass is conserved by streaming, collision and recoloring."""
+    d = _droplet_domain(orc)
+    m0 = d.mass()
+    d.step(30)
+    assert np.all(np.abs(d.mass() - m0) / m0 < 1e-13)
+
+
+def test_per_colour_mass_conserved_with_walls(orc):
+    """P4 with fullway bounce-back walls and a body force (solid cells hold the
+    in-transit populations)."""
+    d = _droplet_domain(orc, bc=(0, 1, 1), force_mode=2, g=(0.0, 0.0, -1e-5))
+    m0 = d.mass()
+    d.step(30)
+    assert np.all(np.abs(d.mass() - m0) / m0 < 1e-13)
+
+
+def test_momentum_balance(orc):
+    """P5: the post-collision momentum of a cell is j + F, so over a periodic
+    domain sum j(t+1) = sum j(t) + sum F(t) (u in Sec. II.A includes F/2)."""
+    d = _droplet_domain(orc, force_mode=1, g=(1e-5, -2e-5, 3e-5))
+    d.step(3)
+
+    def total_j():
+        m = d.macros()
+        rho = m["rho_r"] + m["rho_b"]
+        F = d.field("F")
+        return (rho[None] * m["u"] - F / 2).reshape(3, -1).sum(1), F.reshape(3, -1).sum(1)
+
+    j0, F0 = total_j()
+    d.step(1)
+    j1, _ = total_j()
+    assert np.allclose(j1 - j0, F0, rtol=0, atol=1e-13)
+
+
+def test_uniform_mixture_is_fixed_point(orc):
+    """P6: a uniform state (any u, any colour mix) is a fixed point: the
+    equilibrium central moments do not depend on u (Sec. III.D)."""
+    n = 6
+    ar, ab = inputs.rest_fractions(1.0, 0.1)
+    P = orc.make_params(n, n, n, rho_r0=1.0, rho_b0=0.1, alpha_r=ar, alpha_b=ab,
+                        nu_r=0.05, nu_b=0.1)
+    d = orc.Domain(P)
+    sh = (n, n, n)
+    u = np.empty((3,) + sh)
+    u[0], u[1], u[2] = 0.07, -0.04, 0.02
+    d.init(np.full(sh, 0.6), np.full(sh, 0.03), u)
+    f0 = d.populations()
+    d.step(5)
+    f1 = d.populations()
+    assert max(np.abs(f1[0] - f0[0]).max(), np.abs(f1[1] - f0[1]).max()) < 1e-15
+
+
+def test_taylor_green_decay_rate(orc):
+    """P10: 2D Taylor-Green vortex decays at 2 nu k^2 with nu = (tau - 1/2) c_s^2."""
+    L, nu, U = 32, 0.05, 0.01
+    P = orc.make_params(L, L, 1, nu_r=nu, nu_b=nu, sigma=0.0)
+    d = orc.Domain(P)
+    y, x = np.meshgrid(np.arange(L), np.arange(L), indexing="ij")
+    k = 2 * np.pi / L
+    u = np.zeros((3, 1, L, L))
+    u[0, 0] = U * np.sin(k * x) * np.cos(k * y)
+    u[1, 0] = -U * np.cos(k * x) * np.sin(k * y)
+    d.init(np.full((1, L, L), 0.5), np.full((1, L, L), 0.5), u)
+    d.step(10)
+    a0 = np.abs(d.macros()["u"][0]).max()
+    d.step(400)
+    a1 = np.abs(d.macros()["u"][0]).max()
+    rate = -math.log(a1 / a0) / 400
+    assert abs(rate - 2 * nu * k * k) / (2 * nu * k * k) < 2e-3
+
+
+def test_translation_equivariance(orc):
+    """Periodic wrap: shifting the initial fields shifts the result bit for bit."""
+    n = 10
+    P = orc.make_params(n, n, n, rho_r0=1.0, rho_b0=0.5, alpha_r=1 - 19 / 54,
+                        alpha_b=8 / 27, nu_r=0.05, nu_b=0.07)
+    rr, rb, u = inputs.droplet_fields((n, n, n), (4.3, 5.1, 4.7), 3.0, 1.0, 0.5,
+                                      u0=(0.01, 0.02, -0.01), noise=1e-3, seed=5)
+    shift = (3, 5, 7)  # (z, y, x)
+    outs = []
+    for s in ((0, 0, 0), shift):
+        d = orc.Domain(P)
+        d.init(np.roll(rr, s, (0, 1, 2)), np.roll(rb, s, (0, 1, 2)), np.roll(u, s, (1, 2, 3)))
+        d.step(6)
+        outs.append(d.macros())
+    for key in ("rho_r", "rho_b", "p", "phi"):
+        assert np.array_equal(np.roll(outs[0][key], shift, (0, 1, 2)), outs[1][key])
+    assert np.array_equal(np.roll(outs[0]["u"], shift, (1, 2, 3)), outs[1]["u"])
+
+
+def test_mirror_symmetry(orc):
+    """P11: a state symmetric under x -> -x stays symmetric (u_x antisymmetric)."""
+    n = 12
+    P = orc.make_params(n, n, n, rho_r0=1.0, rho_b0=0.2, alpha_r=1 - 19 / 135,
+                        alpha_b=8 / 27, nu_r=0.05, nu_b=0.07)
+    rr, rb, u = inputs.droplet_fields((n, n, n), (5.5, 6.2, 5.8), 3.5, 1.0, 0.2,
+                                      semi_axes=(3.5, 3.0, 2.6))
+    u[1] = 0.01
+    d = orc.Domain(P)
+    d.init(rr, rb, u)
+    d.step(15)
+    m = d.macros()
+    for key in ("rho_r", "rho_b", "p", "phi"):
+        assert np.abs(m[key] - m[key][:, :, ::-1]).max() < 1e-13
+    assert np.abs(m["u"][0] + m["u"][0][:, :, ::-1]).max() < 1e-14
+    assert np.abs(m["u"][1] - m["u"][1][:, :, ::-1]).max() < 1e-14
+    assert np.abs(m["u"][1]).max() > 1e-3
+
+
+def _layered_run(orc, H, model, use_Q, steps):
+    rr0, rb0, ab = 0.1, 0.8, 0.9       # Case A of the layered-flow table
+    ar = 1 - (1 - ab) / (rr0 / rb0)
+    nz, b = H + 2, H / 2.0
+    a, G, nu = b / 2.0, 1.5e-8, 0.1
+    P = orc.make_params(1, 1, nz, bc=(0, 0, 1), rho_r0=rr0, rho_b0=rb0, alpha_r=ar,
+                        alpha_b=ab, nu_r=nu, nu_b=nu, sigma=0.002 / 4.5, force_mode=1,
+                        g=(G, 0.0, 0.0), model=model, use_Q=use_Q)
+    d = orc.Domain(P)
+    d.init(*inputs.layered_fields(nz, a, rr0, rb0))
+    d.step(steps)
+    ux = d.macros()["u"][0, 1:-1, 0, 0]
+    z = np.arange(1, nz - 1) - (nz - 1) / 2.0
+    mr, mb = rr0 * nu, rb0 * nu
+    A1, A2 = -G / (2 * mr), -G / (2 * mb)
+    C1, C2 = (A2 - A1) * a * a - A2 * b * b, -A2 * b * b
+    ref = np.where(np.abs(z) <= a, A1 * z * z + C1, A2 * z * z + C2)
+    outer = np.abs(z) >= a + 3
+    return ux, ref, outer
+
+
+def test_layered_flow_generalized_vs_standard(orc):
+    """P9 (layered two-phase Poiseuille, Sec. IV.C, Case A): with Model D the
+    heavy layer follows the analytic profile, with Model A it does not; the
+    light-core error shrinks with resolution (diffuse-interface width)."""
+    uxD, ref, outer = _layered_run(orc, 50, 3, 1, 30000)
+    uxA, _, _ = _layered_run(orc, 50, 0, 0, 30000)
+    errD = np.abs(uxD[outer] - ref[outer]).max() / ref.max()
+    errA = np.abs(uxA[outer] - ref[outer]).max() / ref.max()
+    assert errD < 0.01, errD
+    assert errA > 0.15, errA
+    l2_50 = np.linalg.norm(uxD - ref) / np.linalg.norm(ref)
+    ux100, ref100, _ = _layered_run(orc, 100, 3, 1, 60000)
+    l2_100 = np.linalg.norm(ux100 - ref100) / np.linalg.norm(ref100)
+    assert l2_100 < 0.10 and l2_100 < 0.65 * l2_50, (l2_50, l2_100)
+
+
+def test_laplace_law_cylinder(orc):
+    """P8 (stationary droplet, Sec. IV.A): a cylindrical droplet (periodic slab
+    one cell thick) reaches sigma_cal = R dp within 3 % of sigma."""
+    L, R, sigma = 48, 12.0, 0.012
+    P = orc.make_params(L, L, 1, nu_r=1 / 6, nu_b=1 / 6, sigma=sigma)
+    d = orc.Domain(P)
+    d.init(*inputs.droplet_fields((1, L, L), (L / 2 - 0.5, L / 2 - 0.5, 0), R, 1.0, 1.0))
+    d.step(2000)
+    m = d.macros()
+    y, x = np.meshgrid(np.arange(L), np.arange(L), indexing="ij")
+    r = np.hypot(x - L / 2 + 0.5, y - L / 2 + 0.5)
+    p = m["p"][0]
+    Reff = math.sqrt(((1 + m["phi"][0]) / 2).sum() / math.pi)
+    sig = Reff * (p[r < R - 4].mean() - p[r > R + 4].mean())
+    assert abs(sig - sigma) / sigma < 0.03, sig

@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Throughput of the D3Q27 colour-gradient CM-MRT time step on GB300.
+
+Workload: the translating droplet, 128^3 periodic cells, density ratio 10
+(rho_r0 = 1, rho_b0 = 0.1), R = 20, nu = 0.05, sigma = 0.005, beta = 0.7,
+initial velocity (0.05, 0.05, 0), FP32 storage and arithmetic.  One bench step
+is one lattice time step over the whole domain; the metric is million lattice
+updates per second (MLUPS).  With --gpus N (launched by torchrun) every rank
+advances its own independent replica (the method shards into independent
+domains only, so there is no collective on the data path; scaling is weak).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+The reference arm times the FP64 CPU oracle as it stands on the host cores, on
+a bounded periodic slab of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D3Q27 CG-CM MLUPS"
+UNIT = "MLUPS"
+STEP_BYTES_432 = 432          # paper layout: 2 colours x 27 FP32 populations, read + write
+COLLIDE_BYTES_PER_CELL = 248  # k_collide: F in (108) + rho_r, rho_b (8) + F (12) + (p-rho cs2)u (12) + F out (108)
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--edge", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
+    return ap.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(edge):
+    from paper_2309_07801_gb300 import inputs
+    wl = inputs.translating_droplet(edge)
+    return wl, inputs.workload_fields(wl)
+
+
+def describe(wl):
+    return ("translating droplet %d^3 periodic, ratio 10 (1:0.1), R=%g, nu=0.05, sigma=0.005, "
+            "beta=0.7, u0=(0.05,0.05,0), Model D, Q on" % (wl.nx, 20.0 * wl.nx / 128.0))
+
+
+# ---- distributed plumbing (one process per GPU, replicas) -------------------------------
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---- clocks during the timed region ----------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(self.REASONS, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_identifier():
+    import torch
+    try:
+        u = torch.cuda.get_device_properties(torch.cuda.current_device()).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+        return vis or "0"
+
+
+# ---- oracle timing (CPU baseline and the reference arm) ------------------------------------
+
+def oracle_rate(edge_xy, nz, steps, budget=None):
+    """Time the FP64 oracle on a periodic slab edge_xy^2 x nz of the workload."""
+    import oracle
+    from paper_2309_07801_gb300 import inputs
+    wl = inputs.translating_droplet(edge_xy)
+    rr, rb, u = inputs.workload_fields(wl)
+    z0 = wl.nz // 2 - nz // 2
+    sl = slice(z0, z0 + nz)
+    p = wl.params()
+    p["nz"] = nz
+    d = oracle.Domain(oracle.make_params(**p))
+    d.init(np.ascontiguousarray(rr[sl]), np.ascontiguousarray(rb[sl]),
+           np.ascontiguousarray(u[:, sl]))
+    cells = edge_xy * edge_xy * nz
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps:
+        d.step(1)
+        done += 1
+        if budget is not None and time.perf_counter() - t0 > budget:
+            break
+    dt = time.perf_counter() - t0
+    d.close()
+    return cells * done / dt / 1e6, done, dt, cells
+
+
+def cpu_baseline(edge, budget):
+    import oracle
+    oracle.build()
+    nz = max(1, min(edge, 16))
+    mlups, done, dt, cells = oracle_rate(edge, nz, 10 ** 6, budget)
+    return {"value": mlups, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": "%d steps of a %dx%dx%d periodic slab through the droplet of the %d^3 "
+                      "workload (FP64 oracle, %.1f s)" % (done, edge, edge, nz, edge, dt)}
+
+
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return
+    import oracle
+    oracle.build()
+    wl, _ = workload(args.edge)
+    # size the per-step slab so that warmup + steps fit in about two minutes
+    probe, _, _, _ = oracle_rate(args.edge, 1, 2)
+    budget_cells = probe * 1e6 * 120.0 / max(1, args.steps + args.warmup)
+    nz = int(max(1, min(args.edge, budget_cells // (args.edge * args.edge))))
+    if args.warmup > 0:
+        oracle_rate(args.edge, nz, args.warmup)
+    mlups, done, dt, cells = oracle_rate(args.edge, nz, args.steps)
+    cores = oracle.threads()
+    line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / max(1, done) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": describe(wl), "cells": wl.cells, "parallelism": "cpu-oracle"},
+            "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "each step: one step of a %dx%dx%d periodic slab of the "
+                                       "%d^3 workload (%d cells)" % (args.edge, args.edge, nz,
+                                                                     args.edge, cells)},
+            "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- our arm -----------------------------------------------------------------------------
+
+def run_ours(args, dist):
+    import torch
+    from paper_2309_07801_gb300 import build, cg
+    if dist.world == 1:
+        torch.cuda.set_device(0)
+    build.build()
+    wl, (rr, rb, u) = workload(args.edge)
+    params = cg.make_params(precision="f32", **wl.params())
+    N = wl.cells
+    K, W = args.steps, max(3, args.warmup)
+
+    d = cg.Domain(params)
+    stream = d.stream
+    d.init(rr, rb, u)
+    d.step(W)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(gpu_identifier())
+    cg.cg_profile_enable(d.h, K)
+    clocks.start()
+    time.sleep(0.2)
+    d.step(W)  # keep the GPU busy while the sampler starts
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cg.cg_step(d.h, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    ms_total = dist.max(e0.elapsed_time(e1))
+    pass_ms, timed = cg.cg_profile_read(d.h)
+    cg.cg_profile_enable(d.h, 0)
+    mass, nonfinite = d.mass()
+    value = N * K * dist.world / (ms_total * 1e-3) / 1e6
+
+    peak, peak_kind = load_peaks()
+    collide_ms = pass_ms[3] / max(1, timed)
+    achieved = COLLIDE_BYTES_PER_CELL * N / (collide_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_kind": peak_kind, "bytes_per_cell": COLLIDE_BYTES_PER_CELL,
+                "pass_ms_per_step": {cg.PASS_NAMES[i]: pass_ms[i] / max(1, timed) for i in range(4)}}
+    step_roofline = {"bytes_per_cell": STEP_BYTES_432,
+                     "frac": value / dist.world * 1e6 * STEP_BYTES_432 / (peak * 1e9),
+                     "peak": peak, "unit": "GB/s"}
+    d.close()
+
+    # end to end through the C ABI with pinned host buffers: upload the initial
+    # fields, advance K steps, read the macroscopic fields back
+    pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+    h_rr, h_rb, h_u = pin(N), pin(N), pin(3 * N)
+    h_rr[:] = rr.reshape(-1)
+    h_rb[:] = rb.reshape(-1)
+    h_u[:] = u.reshape(-1)
+    o_rr, o_rb, o_u, o_p, o_phi = pin(N), pin(N), pin(3 * N), pin(N), pin(N)
+    d2 = cg.Domain(params)
+    d2.init(h_rr, h_rb, h_u)
+    d2.step(W)
+    torch.cuda.synchronize()
+    dist.barrier()
+    t0 = time.perf_counter()
+    cg.cg_init_fields(d2.h, h_rr, h_rb, h_u)
+    cg.cg_step(d2.h, K)
+    cg.cg_read_macros(d2.h, o_rr, o_rb, o_u, o_p, o_phi)
+    t_e2e = dist.max(time.perf_counter() - t0)
+    d2.close()
+    e2e = {"value": N * K * dist.world / t_e2e / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": 5 * 8 * N / K, "d2h_bytes_per_step": 7 * 8 * N / K,
+           "timed": "cg_init_fields (H2D) + cg_step(K) + cg_read_macros (D2H), host clock"}
+
+    if dist.rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
+            "steps": K, "warmup": W, "ms_per_step": ms_total / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": describe(wl), "cells": N,
+                       "parallelism": "replicas" if dist.world > 1 else "single",
+                       "l2": "inputs larger than L2: population state 2 x %.0f MB" %
+                             (N * 128 / 1e6)},
+            "roofline": roofline, "step_roofline_432B": step_roofline,
+            "e2e": e2e, "gpu_launches": 4 * K, "clocks": clk,
+            "mass": list(map(float, mass)), "nonfinite": nonfinite}
+    if not args.no_cpu_baseline and dist.world == 1:
+        line["cpu_baseline"] = cpu_baseline(args.edge, args.cpu_budget)
+    elif not args.no_cpu_baseline:
+        line["cpu_baseline"] = None
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist)
+        else:
+            run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * cg27.h -- C ABI of the GB300 (sm_103a) implementation of the time step of
+ * the three-dimensional two-component colour-gradient lattice Boltzmann model
+ * with central-moment MRT collision and generalized equilibria
+ * (S. Saito et al., arXiv 2309.07801).
+ *
+ * One time step, in the paper's terms:
+ *   streaming  f_i(x + c_i, t+1) = f_i^*(x, t)                      (Sec. II.A)
+ *   fields     rho_k, rho, rho u = sum f_i c_i + F/2, p, phi       (Sec. II.A)
+ *   interface  grad phi, n, kappa = -div_s n, F_s = sigma kappa grad phi / 2
+ *   correction Q = -3 d_a[(p - rho c_s^2) u_a]                      (Sec. III.E)
+ *   collision  central-moment MRT toward the velocity-independent
+ *              equilibrium central moments                      (Secs. II.B, III.D)
+ *   recoloring f^{r,*}, f^{b,*} with R = beta rho_r rho_b p n / rho^2 (Sec. II.A)
+ *   walls      fullway bounce-back at solid cells                    (Sec. IV)
+ *
+ * Conventions shared by every entry point
+ *   - All values are in lattice units.  Cell (x, y, z) has linear index
+ *     x + nx * (y + ny * z): x is fastest.  Vector fields are passed as three
+ *     consecutive scalar fields (all x components, then y, then z).
+ *   - Host arrays are owned by the caller; the library copies them in or out
+ *     during the call and keeps no host pointer afterwards.
+ *   - Device memory is owned by the caller: cg_workspace_bytes() tells how
+ *     much, the caller allocates it (e.g. a uint8 CUDA tensor) and passes it to
+ *     cg_create().  The library never calls cudaMalloc/cudaFree.
+ *   - Work is enqueued on the CUDA stream given to cg_create() (NULL = the
+ *     legacy default stream).  cg_step() returns without waiting; the read
+ *     calls synchronise that stream before returning.
+ *   - Every function returns CG_OK (0) or a negative CG_ERR_* code; the text of
+ *     the last error of the calling thread is returned by cg_last_error().
+ *     No exception crosses the ABI.
+ *   - Population order at the ABI (cg_read_populations) is the 27-velocity
+ *     order printed in Sec. II.A; the opposite of odd i is i + 1.
+ */
+#ifndef CG27_H
+#define CG27_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CG27_ABI_VERSION 1
+
+/* return codes */
+#define CG_OK 0
+#define CG_ERR_INVALID_ARG (-1) /* bad pointer, size or parameter value */
+#define CG_ERR_UNSUPPORTED (-2) /* valid request this build does not implement */
+#define CG_ERR_CUDA (-3)        /* a CUDA runtime call failed (text has details) */
+#define CG_ERR_NONFINITE (-4)   /* a non-finite density was produced */
+#define CG_ERR_WORKSPACE (-5)   /* workspace missing, too small or misaligned */
+
+/* boundary kind per axis */
+#define CG_BC_PERIODIC 0
+#define CG_BC_BOUNCEBACK 1 /* fullway bounce-back: cells 0 and n-1 are solid */
+
+/* body force added to the interfacial force (Sec. IV test problems) */
+#define CG_FORCE_NONE 0
+#define CG_FORCE_CONST 1    /* F = g                    (layered flow, Sec. IV.C) */
+#define CG_FORCE_GRAVITY 2  /* F = rho g                (rising bubble, Sec. IV.D) */
+#define CG_FORCE_BUOYANCY 3 /* F = (rho - rho_ref) g    (Rayleigh-Taylor, Sec. IV.E) */
+
+/* equilibrium central moments (Table "Summary of equilibria models") */
+#define CG_MODEL_A 0 /* g^{eq,2} + (p - rho cs^2) E_i          (Sec. III.A) */
+#define CG_MODEL_B 1 /* g^{eq,6} + (p - rho cs^2) E_i          (Sec. III.B) */
+#define CG_MODEL_C 2 /* g^{eq,6}, Phi_i up to O(u^3) (Li et al.) (Sec. III.C) */
+#define CG_MODEL_D 3 /* generalized equilibria, Phi_i up to O(u^6) (Sec. III.D) */
+
+/* storage and arithmetic precision */
+#define CG_F64 0 /* FP64 storage and arithmetic */
+#define CG_F32 1 /* FP32 storage and arithmetic */
+
+typedef struct cg_params {
+  int32_t nx, ny, nz;     /* cells per axis, each >= 1 (>= 3 on a bounce-back axis) */
+  int32_t bc[3];          /* CG_BC_* per axis (x, y, z) */
+  double rho_r0, rho_b0;  /* reference densities of the red and blue fluids (> 0) */
+  double alpha_r, alpha_b;/* rest fractions in [0, 1); (c_s^k)^2 = (9/19)(1 - alpha_k) */
+  double nu_r, nu_b;      /* kinematic viscosities (>= 0) */
+  double sigma;           /* interfacial tension coefficient */
+  double beta;            /* recoloring parameter */
+  double omega[11];       /* relaxation rates omega_0..omega_10 of the collision;
+                             omega[1] is ignored (1/tau from the local viscosity) */
+  double g[3];            /* acceleration vector used by the body-force modes */
+  double rho_ref;         /* reference density of CG_FORCE_BUOYANCY */
+  int32_t force_mode;     /* CG_FORCE_* */
+  int32_t model;          /* CG_MODEL_* */
+  int32_t use_Q;          /* 1: apply the correction term Q (Sec. III.E); 0: omit it */
+  int32_t precision;      /* CG_F64 or CG_F32 */
+  int32_t solid_mask;     /* 1: cg_init_fields() may be given a solid mask (reserves
+                             workspace for walls; implied by a bounce-back axis) */
+  int32_t reserved_;      /* must be 0 */
+} cg_params;
+
+typedef struct cg_ctx cg_ctx; /* opaque */
+
+/* Fill *p with the defaults of Sec. III.E: Model D, Q on, all omega = 1,
+ * rho_r0 = rho_b0 = 1, alpha = 8/27, nu = 0.1, sigma = 0, beta = 0.7,
+ * periodic, no body force, FP32, and the given size. */
+int cg_params_default(cg_params *p, int32_t nx, int32_t ny, int32_t nz);
+
+/* Bytes of device workspace a domain with these parameters needs
+ * (populations double-buffered, side fields, reduction scratch). */
+int cg_workspace_bytes(const cg_params *p, size_t *bytes);
+
+/* Create a domain.  d_workspace: device pointer of at least
+ * cg_workspace_bytes() bytes, 256-byte aligned, owned by the caller and kept
+ * alive until cg_destroy().  cuda_stream: a cudaStream_t (may be NULL).
+ * The domain is not usable until cg_init_fields() succeeds. */
+int cg_create(const cg_params *p, void *d_workspace, size_t bytes,
+              void *cuda_stream, cg_ctx **out);
+
+/* Initialise from host fields: rho_r[N], rho_b[N] (> 0 where fluid), u[3N]
+ * (the velocity of the equilibrium), solid[N] (nonzero = solid cell; may be
+ * NULL; non-NULL needs params.solid_mask or a bounce-back axis).  Cells 0
+ * and n-1 of a bounce-back axis are solid whatever the mask.  Every fluid
+ * cell gets the post-collision populations f_i^k = (rho_k / rho)
+ * f_i^eq(rho, p, u) of the selected model; solid cells start empty.  The
+ * first cg_step() begins with streaming. */
+int cg_init_fields(cg_ctx *ctx, const double *rho_r, const double *rho_b,
+                   const double *u, const uint8_t *solid);
+
+/* Advance nsteps (>= 0) time steps, enqueued on the domain's stream. */
+int cg_step(cg_ctx *ctx, int64_t nsteps);
+
+/* Copy the fields of the latest post-streaming state to host arrays (each may
+ * be NULL): rho_r[N], rho_b[N], u[3N] (Eq. for rho u, including F/2), p[N]
+ * (Eq. pressure), phi[N] (Eq. order parameter).  Before the first step these
+ * are the initial fields.  Solid cells report the densities of the populations
+ * they hold and zero for u, p and phi. */
+int cg_read_macros(cg_ctx *ctx, double *rho_r, double *rho_b, double *u,
+                   double *p, double *phi);
+
+/* Copy the post-collision, post-recoloring populations of both colours to host
+ * arrays fr[27N], fb[27N] (population-major: fr[i*N + cell]); either may be
+ * NULL. */
+int cg_read_populations(cg_ctx *ctx, double *fr, double *fb);
+
+/* Per-colour mass (sum over all cells, solid cells included) of the latest
+ * state, accumulated in FP64 in a fixed order; *nonfinite is set to 1 if any
+ * step since cg_init_fields() produced a non-finite density, else 0.  Either
+ * pointer may be NULL. */
+int cg_reduce(cg_ctx *ctx, double out_mass[2], int32_t *nonfinite);
+
+/* Checkpoint: cg_state_bytes() gives the size of an opaque host blob that
+ * cg_save_state() fills and cg_load_state() restores into a domain created
+ * with the same parameters.  A restored domain continues bit for bit. */
+int cg_state_bytes(cg_ctx *ctx, size_t *bytes);
+int cg_save_state(cg_ctx *ctx, void *host, size_t bytes);
+int cg_load_state(cg_ctx *ctx, const void *host, size_t bytes);
+
+/* Steps taken since cg_init_fields() (or as restored by cg_load_state()). */
+int cg_steps_taken(cg_ctx *ctx, int64_t *steps);
+
+/* Per-pass device timing.  cg_profile_enable(ctx, max_steps) makes the next
+ * max_steps calls of the step loop record CUDA events around each of its four
+ * passes (max_steps = 0 turns timing off).  cg_profile_read() synchronises the
+ * stream and returns, for passes 0..3 (streaming + sums, colour gradient,
+ * force/recoloring state, streaming + collision), the summed device time in
+ * milliseconds and the number of timed steps. */
+#define CG_NUM_PASSES 4
+int cg_profile_enable(cg_ctx *ctx, int64_t max_steps);
+int cg_profile_read(cg_ctx *ctx, double ms[CG_NUM_PASSES], int64_t *steps);
+
+/* Release the domain (the workspace stays the caller's). */
+int cg_destroy(cg_ctx *ctx);
+
+/* Text of the last error on the calling thread ("" if none). */
+const char *cg_last_error(void);
+
+/* ABI version of the loaded library (CG27_ABI_VERSION). */
+int cg_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CG27_H */

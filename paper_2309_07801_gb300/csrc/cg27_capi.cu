@@ -1,0 +1,638 @@
+// cg27_capi.cu -- host side of the C ABI declared in include/cg27.h:
+// workspace layout, kernel launches of one time step, initialisation,
+// read-back, reductions and checkpoints.  Device code is in cg27_device.cuh.
+#include "cg27.h"
+#include "cg27_device.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace cg27;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CG_CUDA(expr)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (expr);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(CG_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr size_t ALIGN = 256;
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+// paper velocity order (Sec. II.A) -> lexicographic storage index
+int paper_to_lex(int i) {
+  static const int C[27][3] = {
+      {0, 0, 0},   {1, 0, 0},  {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},  {0, 0, 1},   {0, 0, -1},
+      {1, 1, 0},   {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0},  {0, 1, 1},   {0, -1, -1}, {0, 1, -1},
+      {0, -1, 1},  {1, 0, 1},  {-1, 0, -1}, {1, 0, -1},  {-1, 0, 1},  {1, 1, 1},   {-1, -1, -1},
+      {1, 1, -1},  {-1, -1, 1}, {1, -1, 1}, {-1, 1, -1}, {-1, 1, 1},  {1, -1, -1}};
+  return (C[i][0] + 1) + 3 * (C[i][1] + 1) + 9 * (C[i][2] + 1);
+}
+
+constexpr int RED_THREADS = 256;
+
+struct Layout {
+  long long n = 0, stride = 0;
+  size_t elem = 0;
+  bool solid = false;
+  int red_blocks = 0;
+  size_t f[2] = {0, 0}, s[2] = {0, 0}, aux[2] = {0, 0};
+  size_t mask = 0, mac = 0, phi = 0, grad = 0, nrm = 0, force = 0, wv = 0;
+  size_t partial = 0, flag = 0, result = 0, total = 0;
+};
+
+bool needs_solid(const cg_params& p) {
+  return p.solid_mask != 0 || p.bc[0] == CG_BC_BOUNCEBACK || p.bc[1] == CG_BC_BOUNCEBACK ||
+         p.bc[2] == CG_BC_BOUNCEBACK;
+}
+
+int validate(const cg_params* p) {
+  if (!p) return fail(CG_ERR_INVALID_ARG, "params is NULL");
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(CG_ERR_INVALID_ARG, "nx, ny, nz must be >= 1");
+  if ((long long)p->nx * p->ny * p->nz > (1ll << 31) - 1)
+    return fail(CG_ERR_INVALID_ARG, "more than 2^31-1 cells");
+  if (p->nz > 65535) return fail(CG_ERR_INVALID_ARG, "nz must be <= 65535");
+  const int n[3] = {p->nx, p->ny, p->nz};
+  for (int a = 0; a < 3; ++a) {
+    if (p->bc[a] != CG_BC_PERIODIC && p->bc[a] != CG_BC_BOUNCEBACK)
+      return fail(CG_ERR_INVALID_ARG, "bc must be CG_BC_PERIODIC or CG_BC_BOUNCEBACK");
+    if (p->bc[a] == CG_BC_BOUNCEBACK && n[a] < 3)
+      return fail(CG_ERR_INVALID_ARG, "a bounce-back axis needs at least 3 cells");
+  }
+  if (!(p->rho_r0 > 0) || !(p->rho_b0 > 0)) return fail(CG_ERR_INVALID_ARG, "rho_r0, rho_b0 must be > 0");
+  if (!(p->alpha_r >= 0 && p->alpha_r < 1) || !(p->alpha_b >= 0 && p->alpha_b < 1))
+    return fail(CG_ERR_INVALID_ARG, "alpha_r, alpha_b must be in [0, 1)");
+  if (!(p->nu_r >= 0) || !(p->nu_b >= 0)) return fail(CG_ERR_INVALID_ARG, "viscosities must be >= 0");
+  if (!std::isfinite(p->sigma) || !std::isfinite(p->beta)) return fail(CG_ERR_INVALID_ARG, "sigma, beta must be finite");
+  for (int q = 0; q < 11; ++q)
+    if (!std::isfinite(p->omega[q])) return fail(CG_ERR_INVALID_ARG, "omega must be finite");
+  if (p->force_mode < CG_FORCE_NONE || p->force_mode > CG_FORCE_BUOYANCY)
+    return fail(CG_ERR_INVALID_ARG, "unknown force_mode");
+  if (p->model < CG_MODEL_A || p->model > CG_MODEL_D) return fail(CG_ERR_INVALID_ARG, "unknown model");
+  if (p->precision != CG_F64 && p->precision != CG_F32)
+    return fail(CG_ERR_UNSUPPORTED, "precision must be CG_F64 or CG_F32");
+  if (p->reserved_ != 0) return fail(CG_ERR_INVALID_ARG, "reserved_ must be 0");
+  return CG_OK;
+}
+
+Layout make_layout(const cg_params& p) {
+  Layout L;
+  L.n = (long long)p.nx * p.ny * p.nz;
+  L.stride = (L.n + 63) / 64 * 64;
+  L.elem = (p.precision == CG_F64) ? 8 : 4;
+  L.solid = needs_solid(p);
+  L.red_blocks = (int)std::min<long long>(1024, (L.n + RED_THREADS - 1) / RED_THREADS);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  };
+  const size_t field = (size_t)L.stride * L.elem;
+  for (int b = 0; b < 2; ++b) L.f[b] = take(27 * field);
+  for (int b = 0; b < 2; ++b) L.s[b] = take(5 * field);
+  if (L.solid) {
+    for (int b = 0; b < 2; ++b) L.aux[b] = take(27 * field);
+    L.mask = take((size_t)L.stride * 4);
+  }
+  L.mac = take(5 * field);
+  L.phi = take(field);
+  L.grad = take(3 * field);
+  L.nrm = take(3 * field);
+  L.force = take(3 * field);
+  L.wv = take(3 * field);
+  L.partial = take((size_t)L.red_blocks * 2 * sizeof(double));
+  L.flag = take(sizeof(unsigned int));
+  L.result = take(2 * sizeof(double));
+  L.total = off;
+  return L;
+}
+
+dim3 block_of(const cg_params& p) {
+  int bx = p.nx >= 128 ? 128 : (p.nx >= 64 ? 64 : 32);
+  return dim3(bx, 128 / bx, 1);
+}
+
+}  // namespace
+
+struct cg_ctx {
+  cg_params prm;
+  Layout L;
+  char* ws = nullptr;
+  cudaStream_t stream = nullptr;
+  int64_t steps = 0;
+  bool initialised = false;
+  bool unit = false;  // all omega = 1 except omega_1, Model D: the Sec. III.E form
+  // per-pass timing: events[5 * s + k] brackets pass k of timed step s
+  std::vector<cudaEvent_t> events;
+  int64_t prof_capacity = 0, prof_used = 0;
+  ~cg_ctx() {
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+template <typename T>
+Phys<T> make_phys(const cg_params& p) {
+  Phys<T> ph;
+  const double xi = 9.0 / 19.0;
+  ph.rho_r0 = T(p.rho_r0);
+  ph.rho_b0 = T(p.rho_b0);
+  ph.cr2 = T(xi * (1.0 - p.alpha_r));
+  ph.cb2 = T(xi * (1.0 - p.alpha_b));
+  ph.nu_r = T(p.nu_r);
+  ph.nu_b = T(p.nu_b);
+  ph.sigma = T(p.sigma);
+  ph.beta = T(p.beta);
+  for (int q = 0; q < 11; ++q) ph.om[q] = T(p.omega[q]);
+  for (int a = 0; a < 3; ++a) ph.g[a] = T(p.g[a]);
+  ph.rho_ref = T(p.rho_ref);
+  ph.force_mode = p.force_mode;
+  ph.model = p.model;
+  ph.use_Q = p.use_Q;
+  return ph;
+}
+
+Geom make_geom(const cg_ctx* c) {
+  Geom g;
+  g.nx = c->prm.nx;
+  g.ny = c->prm.ny;
+  g.nz = c->prm.nz;
+  g.nxy = c->prm.nx * c->prm.ny;
+  g.stride = c->L.stride;
+  return g;
+}
+
+dim3 grid_of(const cg_params& p, dim3 b) {
+  return dim3((p.nx + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, p.nz);
+}
+
+// pointers for a step that reads buffer `cur` and writes buffer 1 - cur
+template <typename T>
+Ptrs<T> make_ptrs(const cg_ctx* c, int cur) {
+  const Layout& L = c->L;
+  Ptrs<T> P;
+  char* w = c->ws;
+  P.f_in = reinterpret_cast<const T*>(w + L.f[cur]);
+  P.f_out = reinterpret_cast<T*>(w + L.f[1 - cur]);
+  P.s_in = reinterpret_cast<const T*>(w + L.s[cur]);
+  P.s_out = reinterpret_cast<T*>(w + L.s[1 - cur]);
+  P.aux_in = L.solid ? reinterpret_cast<const T*>(w + L.aux[cur]) : nullptr;
+  P.aux_out = L.solid ? reinterpret_cast<T*>(w + L.aux[1 - cur]) : nullptr;
+  P.mask = L.solid ? reinterpret_cast<const uint32_t*>(w + L.mask) : nullptr;
+  P.mac = reinterpret_cast<T*>(w + L.mac);
+  P.phi = reinterpret_cast<T*>(w + L.phi);
+  P.grad = reinterpret_cast<T*>(w + L.grad);
+  P.nrm = reinterpret_cast<T*>(w + L.nrm);
+  P.force = reinterpret_cast<T*>(w + L.force);
+  P.wv = reinterpret_cast<T*>(w + L.wv);
+  P.flag = reinterpret_cast<unsigned int*>(w + L.flag);
+  return P;
+}
+
+template <typename T, bool SOLID>
+void enqueue_step(cg_ctx* c) {
+  const int cur = (int)(c->steps & 1);
+  const Geom g = make_geom(c);
+  const dim3 b = block_of(c->prm), gr = grid_of(c->prm, b);
+  const Ptrs<T> P = make_ptrs<T>(c, cur);
+  const Phys<T> ph = make_phys<T>(c->prm);
+  cudaEvent_t* ev = nullptr;
+  if (c->prof_used < c->prof_capacity) ev = &c->events[5 * c->prof_used++];
+  if (ev) cudaEventRecord(ev[0], c->stream);
+  k_macro<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph);
+  if (ev) cudaEventRecord(ev[1], c->stream);
+  k_normal<T, SOLID><<<gr, b, 0, c->stream>>>(g, P);
+  if (ev) cudaEventRecord(ev[2], c->stream);
+  k_force<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph);
+  if (ev) cudaEventRecord(ev[3], c->stream);
+  if (c->unit)
+    k_collide<T, SOLID, true><<<gr, b, 0, c->stream>>>(g, P, ph);
+  else
+    k_collide<T, SOLID, false><<<gr, b, 0, c->stream>>>(g, P, ph);
+  if (ev) cudaEventRecord(ev[4], c->stream);
+}
+
+template <typename T>
+void enqueue_step_any(cg_ctx* c) {
+  if (c->L.solid)
+    enqueue_step<T, true>(c);
+  else
+    enqueue_step<T, false>(c);
+}
+
+// the population buffer not holding the current state: free between steps
+char* scratch_of(const cg_ctx* c) { return c->ws + c->L.f[1 - (int)(c->steps & 1)]; }
+
+template <typename T, bool SOLID>
+void enqueue_init(cg_ctx* c, const double* d_in) {
+  const Geom g = make_geom(c);
+  const dim3 b = block_of(c->prm), gr = grid_of(c->prm, b);
+  // the initial state is written to buffer 0 (read by the first step)
+  Ptrs<T> P = make_ptrs<T>(c, 1);
+  const long long n = c->L.n;
+  k_init<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, make_phys<T>(c->prm), d_in, d_in + n, d_in + 2 * n, n);
+}
+
+}  // namespace
+
+// ---- solid flags (non-template kernels) -------------------------------------------
+
+namespace cg27 {
+__global__ void k_solid_self(Geom g, uint8_t* solid, int has_user, int bx, int by, int bz) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= g.nx || y >= g.ny) return;
+  const int i = x + g.nx * y + g.nxy * z;
+  uint8_t s = has_user ? (solid[i] != 0) : 0;
+  if (bx && (x == 0 || x == g.nx - 1)) s = 1;
+  if (by && (y == 0 || y == g.ny - 1)) s = 1;
+  if (bz && (z == 0 || z == g.nz - 1)) s = 1;
+  solid[i] = s;
+}
+
+__global__ void k_solid_mask(Geom g, const uint8_t* solid, uint32_t* mask) {
+  Cell c;
+  if (!make_cell(g, c)) return;
+  uint32_t m = solid[c.idx] ? (1u << SELF_SOLID_BIT) : 0u;
+#pragma unroll
+  for (int q = 0; q < 27; ++q)
+    if (solid[nbr(c, CX(q), CY(q), CZ(q))]) m |= (1u << q);
+  mask[c.idx] = m;
+}
+
+__global__ void k_mass_final(const double* partial, int nblocks, double* out) {
+  __shared__ double sr[256], sb[256];
+  double ar = 0.0, ab = 0.0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+    ar += partial[2 * i];
+    ab += partial[2 * i + 1];
+  }
+  sr[threadIdx.x] = ar;
+  sb[threadIdx.x] = ab;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sr[threadIdx.x] += sr[threadIdx.x + s];
+      sb[threadIdx.x] += sb[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = sr[0];
+    out[1] = sb[0];
+  }
+}
+}  // namespace cg27
+
+// ---- C ABI --------------------------------------------------------------------------
+
+extern "C" {
+
+int cg_abi_version(void) { return CG27_ABI_VERSION; }
+
+const char* cg_last_error(void) { return g_err.c_str(); }
+
+int cg_params_default(cg_params* p, int32_t nx, int32_t ny, int32_t nz) {
+  if (!p) return fail(CG_ERR_INVALID_ARG, "params is NULL");
+  std::memset(p, 0, sizeof(*p));
+  p->nx = nx;
+  p->ny = ny;
+  p->nz = nz;
+  p->rho_r0 = p->rho_b0 = 1.0;
+  p->alpha_r = p->alpha_b = 8.0 / 27.0;
+  p->nu_r = p->nu_b = 0.1;
+  p->sigma = 0.0;
+  p->beta = 0.7;
+  for (int q = 0; q < 11; ++q) p->omega[q] = 1.0;
+  p->force_mode = CG_FORCE_NONE;
+  p->model = CG_MODEL_D;
+  p->use_Q = 1;
+  p->precision = CG_F32;
+  return CG_OK;
+}
+
+int cg_workspace_bytes(const cg_params* p, size_t* bytes) {
+  int rc = validate(p);
+  if (rc) return rc;
+  if (!bytes) return fail(CG_ERR_INVALID_ARG, "bytes is NULL");
+  *bytes = make_layout(*p).total;
+  return CG_OK;
+}
+
+int cg_create(const cg_params* p, void* d_workspace, size_t bytes, void* cuda_stream, cg_ctx** out) {
+  int rc = validate(p);
+  if (rc) return rc;
+  if (!out) return fail(CG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  Layout L = make_layout(*p);
+  if (!d_workspace) return fail(CG_ERR_WORKSPACE, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(d_workspace) % ALIGN != 0)
+    return fail(CG_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  if (bytes < L.total)
+    return fail(CG_ERR_WORKSPACE, "workspace too small: need " + std::to_string(L.total) + " bytes");
+  cudaPointerAttributes attr;
+  CG_CUDA(cudaPointerGetAttributes(&attr, d_workspace));
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+    return fail(CG_ERR_WORKSPACE, "workspace is not device memory");
+  cg_ctx* c = new cg_ctx;
+  c->prm = *p;
+  c->L = L;
+  c->ws = static_cast<char*>(d_workspace);
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  bool unit = (p->model == CG_MODEL_D);
+  for (int q = 0; q < 11; ++q)
+    if (q != 1 && p->omega[q] != 1.0) unit = false;
+  c->unit = unit;
+  *out = c;
+  return CG_OK;
+}
+
+int cg_destroy(cg_ctx* c) {
+  delete c;
+  return CG_OK;
+}
+
+int cg_init_fields(cg_ctx* c, const double* rho_r, const double* rho_b, const double* u,
+                   const uint8_t* solid) {
+  if (!c) return fail(CG_ERR_INVALID_ARG, "ctx is NULL");
+  if (!rho_r || !rho_b || !u) return fail(CG_ERR_INVALID_ARG, "rho_r, rho_b, u must be non-NULL");
+  if (solid && !c->L.solid)
+    return fail(CG_ERR_INVALID_ARG, "a solid mask needs params.solid_mask = 1 or a bounce-back axis");
+  const long long n = c->L.n;
+  for (long long i = 0; i < n; ++i) {
+    if (!(std::isfinite(rho_r[i]) && std::isfinite(rho_b[i]) && rho_r[i] >= 0 && rho_b[i] >= 0))
+      return fail(CG_ERR_INVALID_ARG, "densities must be finite and >= 0 (cell " + std::to_string(i) + ")");
+  }
+  c->steps = 0;  // staging lives in population buffer 1, the state goes to buffer 0
+  char* stage = scratch_of(c);
+  double* d_in = reinterpret_cast<double*>(stage);
+  const size_t dbytes = (size_t)n * sizeof(double);
+  CG_CUDA(cudaMemcpyAsync(d_in, rho_r, dbytes, cudaMemcpyHostToDevice, c->stream));
+  CG_CUDA(cudaMemcpyAsync(d_in + n, rho_b, dbytes, cudaMemcpyHostToDevice, c->stream));
+  CG_CUDA(cudaMemcpyAsync(d_in + 2 * n, u, 3 * dbytes, cudaMemcpyHostToDevice, c->stream));
+  const Geom g = make_geom(c);
+  const dim3 b = block_of(c->prm), gr = grid_of(c->prm, b);
+  if (c->L.solid) {
+    uint8_t* d_solid = reinterpret_cast<uint8_t*>(stage + align_up(5 * dbytes));
+    if (solid)
+      CG_CUDA(cudaMemcpyAsync(d_solid, solid, (size_t)n, cudaMemcpyHostToDevice, c->stream));
+    k_solid_self<<<gr, b, 0, c->stream>>>(g, d_solid, solid ? 1 : 0, c->prm.bc[0] == CG_BC_BOUNCEBACK,
+                                          c->prm.bc[1] == CG_BC_BOUNCEBACK, c->prm.bc[2] == CG_BC_BOUNCEBACK);
+    k_solid_mask<<<gr, b, 0, c->stream>>>(g, d_solid, reinterpret_cast<uint32_t*>(c->ws + c->L.mask));
+  }
+  if (c->prm.precision == CG_F64) {
+    if (c->L.solid) enqueue_init<double, true>(c, d_in); else enqueue_init<double, false>(c, d_in);
+  } else {
+    if (c->L.solid) enqueue_init<float, true>(c, d_in); else enqueue_init<float, false>(c, d_in);
+  }
+  CG_CUDA(cudaMemsetAsync(c->ws + c->L.flag, 0, sizeof(unsigned int), c->stream));
+  CG_CUDA(cudaGetLastError());
+  // the host arrays may be pageable and reused by the caller: finish the copies
+  CG_CUDA(cudaStreamSynchronize(c->stream));
+  c->initialised = true;
+  return CG_OK;
+}
+
+int cg_step(cg_ctx* c, int64_t nsteps) {
+  if (!c) return fail(CG_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->initialised) return fail(CG_ERR_INVALID_ARG, "cg_init_fields() has not been called");
+  if (nsteps < 0) return fail(CG_ERR_INVALID_ARG, "nsteps must be >= 0");
+  for (int64_t s = 0; s < nsteps; ++s) {
+    if (c->prm.precision == CG_F64)
+      enqueue_step_any<double>(c);
+    else
+      enqueue_step_any<float>(c);
+    ++c->steps;
+  }
+  CG_CUDA(cudaGetLastError());
+  return CG_OK;
+}
+
+int cg_read_macros(cg_ctx* c, double* rho_r, double* rho_b, double* u, double* p, double* phi) {
+  if (!c) return fail(CG_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->initialised) return fail(CG_ERR_INVALID_ARG, "cg_init_fields() has not been called");
+  const long long n = c->L.n;
+  double* d_out = reinterpret_cast<double*>(scratch_of(c));
+  const Geom g = make_geom(c);
+  const dim3 b = block_of(c->prm), gr = grid_of(c->prm, b);
+  const int cur = (int)(c->steps & 1);
+  if (c->prm.precision == CG_F64) {
+    auto P = make_ptrs<double>(c, cur);
+    if (c->L.solid) k_read_macros<double, true><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), d_out, n);
+    else k_read_macros<double, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), d_out, n);
+  } else {
+    auto P = make_ptrs<float>(c, cur);
+    if (c->L.solid) k_read_macros<float, true><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), d_out, n);
+    else k_read_macros<float, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), d_out, n);
+  }
+  CG_CUDA(cudaGetLastError());
+  const size_t db = (size_t)n * sizeof(double);
+  if (rho_r) CG_CUDA(cudaMemcpyAsync(rho_r, d_out, db, cudaMemcpyDeviceToHost, c->stream));
+  if (rho_b) CG_CUDA(cudaMemcpyAsync(rho_b, d_out + n, db, cudaMemcpyDeviceToHost, c->stream));
+  if (u) CG_CUDA(cudaMemcpyAsync(u, d_out + 2 * n, 3 * db, cudaMemcpyDeviceToHost, c->stream));
+  if (p) CG_CUDA(cudaMemcpyAsync(p, d_out + 5 * n, db, cudaMemcpyDeviceToHost, c->stream));
+  if (phi) CG_CUDA(cudaMemcpyAsync(phi, d_out + 6 * n, db, cudaMemcpyDeviceToHost, c->stream));
+  CG_CUDA(cudaStreamSynchronize(c->stream));
+  return CG_OK;
+}
+
+int cg_read_populations(cg_ctx* c, double* fr, double* fb) {
+  if (!c) return fail(CG_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->initialised) return fail(CG_ERR_INVALID_ARG, "cg_init_fields() has not been called");
+  const long long n = c->L.n;
+  double* d_out = reinterpret_cast<double*>(scratch_of(c));
+  const Geom g = make_geom(c);
+  const dim3 b = block_of(c->prm), gr = grid_of(c->prm, b);
+  // the current state sits in buffer `cur`: read it through the "input" pointers
+  const int cur = (int)(c->steps & 1);
+  const size_t db = (size_t)n * sizeof(double);
+  for (int i = 0; i < 27; ++i) {
+    const int q = paper_to_lex(i);
+    if (c->prm.precision == CG_F64) {
+      auto P = make_ptrs<double>(c, cur);
+      if (c->L.solid) k_read_pop<double, true><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + n);
+      else k_read_pop<double, false><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + n);
+    } else {
+      auto P = make_ptrs<float>(c, cur);
+      if (c->L.solid) k_read_pop<float, true><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + n);
+      else k_read_pop<float, false><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + n);
+    }
+    CG_CUDA(cudaGetLastError());
+    if (fr) CG_CUDA(cudaMemcpyAsync(fr + (size_t)i * n, d_out, db, cudaMemcpyDeviceToHost, c->stream));
+    if (fb) CG_CUDA(cudaMemcpyAsync(fb + (size_t)i * n, d_out + n, db, cudaMemcpyDeviceToHost, c->stream));
+    CG_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  return CG_OK;
+}
+
+int cg_reduce(cg_ctx* c, double out_mass[2], int32_t* nonfinite) {
+  if (!c) return fail(CG_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->initialised) return fail(CG_ERR_INVALID_ARG, "cg_init_fields() has not been called");
+  const Geom g = make_geom(c);
+  double* partial = reinterpret_cast<double*>(c->ws + c->L.partial);
+  double* result = reinterpret_cast<double*>(c->ws + c->L.result);
+  if (c->prm.precision == CG_F64)
+    k_mass_partial<double><<<c->L.red_blocks, RED_THREADS, 0, c->stream>>>(
+        g, reinterpret_cast<const double*>(c->ws + c->L.mac), c->L.n, partial);
+  else
+    k_mass_partial<float><<<c->L.red_blocks, RED_THREADS, 0, c->stream>>>(
+        g, reinterpret_cast<const float*>(c->ws + c->L.mac), c->L.n, partial);
+  k_mass_final<<<1, RED_THREADS, 0, c->stream>>>(partial, c->L.red_blocks, result);
+  CG_CUDA(cudaGetLastError());
+  double m[2];
+  unsigned int flag = 0;
+  CG_CUDA(cudaMemcpyAsync(m, result, sizeof(m), cudaMemcpyDeviceToHost, c->stream));
+  CG_CUDA(cudaMemcpyAsync(&flag, c->ws + c->L.flag, sizeof(flag), cudaMemcpyDeviceToHost, c->stream));
+  CG_CUDA(cudaStreamSynchronize(c->stream));
+  if (out_mass) {
+    out_mass[0] = m[0];
+    out_mass[1] = m[1];
+  }
+  if (nonfinite) *nonfinite = flag ? 1 : 0;
+  return CG_OK;
+}
+
+int cg_profile_enable(cg_ctx* c, int64_t max_steps) {
+  if (!c) return fail(CG_ERR_INVALID_ARG, "ctx is NULL");
+  if (max_steps < 0 || max_steps > (1 << 20)) return fail(CG_ERR_INVALID_ARG, "max_steps out of range");
+  CG_CUDA(cudaStreamSynchronize(c->stream));
+  while ((int64_t)c->events.size() < 5 * max_steps) {
+    cudaEvent_t e;
+    CG_CUDA(cudaEventCreate(&e));
+    c->events.push_back(e);
+  }
+  c->prof_capacity = max_steps;
+  c->prof_used = 0;
+  return CG_OK;
+}
+
+int cg_profile_read(cg_ctx* c, double ms[CG_NUM_PASSES], int64_t* steps) {
+  if (!c) return fail(CG_ERR_INVALID_ARG, "ctx is NULL");
+  CG_CUDA(cudaStreamSynchronize(c->stream));
+  double acc[CG_NUM_PASSES] = {0, 0, 0, 0};
+  for (int64_t s = 0; s < c->prof_used; ++s)
+    for (int k = 0; k < CG_NUM_PASSES; ++k) {
+      float t = 0.f;
+      CG_CUDA(cudaEventElapsedTime(&t, c->events[5 * s + k], c->events[5 * s + k + 1]));
+      acc[k] += t;
+    }
+  if (ms)
+    for (int k = 0; k < CG_NUM_PASSES; ++k) ms[k] = acc[k];
+  if (steps) *steps = c->prof_used;
+  return CG_OK;
+}
+
+int cg_steps_taken(cg_ctx* c, int64_t* steps) {
+  if (!c || !steps) return fail(CG_ERR_INVALID_ARG, "NULL argument");
+  *steps = c->steps;
+  return CG_OK;
+}
+
+// ---- checkpoints -------------------------------------------------------------------------
+
+namespace {
+struct StateHeader {
+  char magic[8];
+  int32_t abi, nx, ny, nz, precision, solid;
+  int64_t steps;
+  uint64_t payload;
+};
+
+// (offset, bytes) of each region saved in a checkpoint, for the current buffer
+int state_regions(const cg_ctx* c, size_t off[6], size_t len[6]) {
+  const Layout& L = c->L;
+  const int cur = (int)(c->steps & 1);
+  const size_t field = (size_t)L.stride * L.elem;
+  int k = 0;
+  off[k] = L.f[cur]; len[k++] = 27 * field;
+  off[k] = L.s[cur]; len[k++] = 5 * field;
+  off[k] = L.mac; len[k++] = 5 * field;
+  off[k] = L.force; len[k++] = 3 * field;
+  if (L.solid) {
+    off[k] = L.aux[cur]; len[k++] = 27 * field;
+    off[k] = L.mask; len[k++] = (size_t)L.stride * 4;
+  }
+  return k;
+}
+}  // namespace
+
+int cg_state_bytes(cg_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return fail(CG_ERR_INVALID_ARG, "NULL argument");
+  size_t off[6], len[6];
+  int k = state_regions(c, off, len);
+  size_t total = sizeof(StateHeader);
+  for (int i = 0; i < k; ++i) total += len[i];
+  *bytes = total;
+  return CG_OK;
+}
+
+int cg_save_state(cg_ctx* c, void* host, size_t bytes) {
+  if (!c || !host) return fail(CG_ERR_INVALID_ARG, "NULL argument");
+  if (!c->initialised) return fail(CG_ERR_INVALID_ARG, "cg_init_fields() has not been called");
+  size_t need = 0;
+  cg_state_bytes(c, &need);
+  if (bytes < need) return fail(CG_ERR_INVALID_ARG, "buffer too small: need " + std::to_string(need));
+  StateHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "CG27STAT", 8);
+  h.abi = CG27_ABI_VERSION;
+  h.nx = c->prm.nx; h.ny = c->prm.ny; h.nz = c->prm.nz;
+  h.precision = c->prm.precision;
+  h.solid = c->L.solid;
+  h.steps = c->steps;
+  h.payload = need - sizeof(StateHeader);
+  std::memcpy(host, &h, sizeof(h));
+  size_t off[6], len[6];
+  int k = state_regions(c, off, len);
+  char* dst = static_cast<char*>(host) + sizeof(h);
+  for (int i = 0; i < k; ++i) {
+    CG_CUDA(cudaMemcpyAsync(dst, c->ws + off[i], len[i], cudaMemcpyDeviceToHost, c->stream));
+    dst += len[i];
+  }
+  CG_CUDA(cudaStreamSynchronize(c->stream));
+  return CG_OK;
+}
+
+int cg_load_state(cg_ctx* c, const void* host, size_t bytes) {
+  if (!c || !host) return fail(CG_ERR_INVALID_ARG, "NULL argument");
+  if (bytes < sizeof(StateHeader)) return fail(CG_ERR_INVALID_ARG, "buffer too small");
+  StateHeader h;
+  std::memcpy(&h, host, sizeof(h));
+  if (std::memcmp(h.magic, "CG27STAT", 8) != 0 || h.abi != CG27_ABI_VERSION)
+    return fail(CG_ERR_INVALID_ARG, "not a checkpoint of this library version");
+  if (h.nx != c->prm.nx || h.ny != c->prm.ny || h.nz != c->prm.nz || h.precision != c->prm.precision ||
+      h.solid != (int)c->L.solid)
+    return fail(CG_ERR_INVALID_ARG, "checkpoint does not match the domain parameters");
+  c->steps = h.steps;  // selects the buffer the regions go to
+  size_t off[6], len[6];
+  int k = state_regions(c, off, len);
+  size_t need = sizeof(h);
+  for (int i = 0; i < k; ++i) need += len[i];
+  if (bytes < need || h.payload != need - sizeof(h)) return fail(CG_ERR_INVALID_ARG, "checkpoint size mismatch");
+  const char* src = static_cast<const char*>(host) + sizeof(h);
+  for (int i = 0; i < k; ++i) {
+    CG_CUDA(cudaMemcpyAsync(c->ws + off[i], src, len[i], cudaMemcpyHostToDevice, c->stream));
+    src += len[i];
+  }
+  CG_CUDA(cudaMemsetAsync(c->ws + c->L.flag, 0, sizeof(unsigned int), c->stream));
+  CG_CUDA(cudaStreamSynchronize(c->stream));
+  c->initialised = true;
+  return CG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,712 @@
+// cg27_device.cuh -- device code of the D3Q27 colour-gradient CM-MRT step
+// (arXiv 2309.07801) for sm_103a.
+//
+// Data layout in device memory (structure of arrays, x fastest, each scalar
+// field `stride` elements long):
+//   F[27]   post-collision total populations f_i^* (two ping-pong copies);
+//           at solid cells the same slots hold the red part of the stored
+//           (bounced) populations;
+//   S[5]    recoloring state of each cell: rho_r/rho, rho_b/rho, R_x, R_y, R_z
+//           (two ping-pong copies).  The two-colour post-collision
+//           populations of Eq. (recoloring) are f^{r,*}_i = (rho_r/rho) f_i^*
+//           + (w_i/c_s^2) c_i.R and f^{b,*}_i = (rho_b/rho) f_i^* - (w_i/c_s^2)
+//           c_i.R, so (F, S) holds the full two-colour state in 27 + 5 values;
+//   AUX[27] blue part at solid cells (only with walls, two copies);
+//   MASK    per cell: bit q set when the neighbour x + c_q is solid, bit 27
+//           when the cell itself is solid (only with walls);
+//   MAC[5]  rho_r, rho_b, j_x, j_y, j_z of the post-streaming state;
+//   PHI     order parameter; GRAD[3], NRM[3] colour gradient and unit normal;
+//   FORCE[3] total force; WV[3] (p - rho c_s^2) u for the correction term.
+// Lattice directions are stored in the lexicographic order
+// q = (c_x+1) + 3 (c_y+1) + 9 (c_z+1); moments use r = a + 3 b + 9 c.
+//
+// One step is four passes (each a kernel over all cells):
+//   k_macro   pull-stream the two colours, sum densities and momentum;
+//   k_normal  isotropic gradient of phi and the unit normal;
+//   k_force   curvature, CSF + body force, velocity, (p - rho c_s^2) u,
+//             recoloring vector R and fractions for the next state;
+//   k_collide pull-stream the totals, correction term Q, CM-MRT collision,
+//             store f^* (recoloring is applied by the next pull).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cg27 {
+
+// ---- lattice ---------------------------------------------------------------
+
+__host__ __device__ constexpr int CX(int q) { return q % 3 - 1; }
+__host__ __device__ constexpr int CY(int q) { return (q / 3) % 3 - 1; }
+__host__ __device__ constexpr int CZ(int q) { return q / 9 - 1; }
+__host__ __device__ constexpr int OPP(int q) { return 26 - q; }
+__host__ __device__ constexpr int CC(int q) { return CX(q) * CX(q) + CY(q) * CY(q) + CZ(q) * CZ(q); }
+__host__ __device__ constexpr int CA(int q, int a) { return a == 0 ? CX(q) : (a == 1 ? CY(q) : CZ(q)); }
+__host__ __device__ constexpr int KI(int a, int b, int c) { return a + 3 * b + 9 * c; }
+constexpr int REST = 13;
+constexpr int SELF_SOLID_BIT = 27;
+
+// D3Q27 weights by |c|^2 (Sec. II.A)
+template <typename T>
+__host__ __device__ constexpr T WQ(int q) {
+  return CC(q) == 0 ? T(8) / T(27)
+                    : (CC(q) == 1 ? T(2) / T(27) : (CC(q) == 2 ? T(1) / T(54) : T(1) / T(216)));
+}
+
+template <typename T>
+struct Lat {
+  static constexpr T CS2 = T(1) / T(3);  // lattice speed of sound squared
+  static constexpr T CS4 = CS2 * CS2;
+};
+
+// ---- kernel arguments --------------------------------------------------------
+
+struct Geom {
+  int nx, ny, nz, nxy;
+  long long stride;  // elements between consecutive scalar fields
+};
+
+template <typename T>
+struct Ptrs {
+  const T* f_in;
+  T* f_out;
+  const T* s_in;
+  T* s_out;
+  const T* aux_in;
+  T* aux_out;
+  const uint32_t* mask;
+  T* mac;
+  T* phi;
+  T* grad;
+  T* nrm;
+  T* force;
+  T* wv;
+  unsigned int* flag;
+};
+
+template <typename T>
+struct Phys {
+  T rho_r0, rho_b0;
+  T cr2, cb2;  // (c_s^k)^2 = xi (1 - alpha_k)
+  T nu_r, nu_b;
+  T sigma, beta;
+  T om[11];
+  T g[3];
+  T rho_ref;
+  int force_mode, model, use_Q;
+};
+
+// ---- cell addressing -----------------------------------------------------------
+
+struct Cell {
+  int idx;
+  int xs[3], ys[3], zs[3];  // offsets of x-1, x, x+1 (etc.) with periodic wrap
+};
+
+__device__ __forceinline__ bool make_cell(const Geom& g, Cell& c) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= g.nx || y >= g.ny) return false;
+  c.xs[0] = (x == 0 ? g.nx - 1 : x - 1);
+  c.xs[1] = x;
+  c.xs[2] = (x == g.nx - 1 ? 0 : x + 1);
+  c.ys[0] = (y == 0 ? g.ny - 1 : y - 1) * g.nx;
+  c.ys[1] = y * g.nx;
+  c.ys[2] = (y == g.ny - 1 ? 0 : y + 1) * g.nx;
+  c.zs[0] = (z == 0 ? g.nz - 1 : z - 1) * g.nxy;
+  c.zs[1] = z * g.nxy;
+  c.zs[2] = (z == g.nz - 1 ? 0 : z + 1) * g.nxy;
+  c.idx = x + c.ys[1] + c.zs[1];
+  return true;
+}
+
+// index of the cell x + (dx, dy, dz), each in {-1, 0, 1}
+__device__ __forceinline__ int nbr(const Cell& c, int dx, int dy, int dz) {
+  return c.xs[dx + 1] + c.ys[dy + 1] + c.zs[dz + 1];
+}
+
+template <typename T>
+__device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
+
+// ---- pull of one direction with the colour split of Eq. (recoloring) -------------
+
+template <typename T, bool SOLID>
+__device__ __forceinline__ void pull_colour(const Ptrs<T>& P, long long stride, int q, int src,
+                                            uint32_t mask, T& fr, T& fb, T& ft) {
+  const T f = ld(P.f_in + q * stride + src);
+  if (SOLID && ((mask >> OPP(q)) & 1u)) {
+    // the source is solid: it stores the red part in F and the blue part in AUX
+    fr = f;
+    fb = ld(P.aux_in + q * stride + src);
+    ft = fr + fb;
+  } else {
+    const T a = ld(P.s_in + src);
+    const T b = ld(P.s_in + stride + src);
+    T t = T(0);
+    if (q != REST) {
+      T cR = T(0);
+      if (CX(q) != 0) cR += T(CX(q)) * ld(P.s_in + 2 * stride + src);
+      if (CY(q) != 0) cR += T(CY(q)) * ld(P.s_in + 3 * stride + src);
+      if (CZ(q) != 0) cR += T(CZ(q)) * ld(P.s_in + 4 * stride + src);
+      t = (WQ<T>(q) / Lat<T>::CS2) * cR;
+    }
+    fr = a * f + t;
+    fb = b * f - t;
+    ft = f;
+  }
+}
+
+// ---- order parameter, Eq. (order parameter) --------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T order_parameter(T rr, T rb, const Phys<T>& ph) {
+  const T a = rr / ph.rho_r0, b = rb / ph.rho_b0;
+  return (a + b > T(0)) ? (a - b) / (a + b) : T(0);
+}
+
+// ---- factorised central-moment transforms ---------------------------------------
+// One axis: values at c = -1, 0, +1 <-> central moments of order 0, 1, 2 about u.
+// Forward: k0 = sum f, k1 = sum f (c-u), k2 = sum f (c-u)^2.
+template <typename T>
+__device__ __forceinline__ void fwd3(T& fm, T& fz, T& fp, T u) {
+  const T s = fp + fm, d = fp - fm;
+  const T k0 = s + fz;
+  const T k1 = d - u * k0;
+  const T k2 = s - u * (d + k1);
+  fm = k0;
+  fz = k1;
+  fp = k2;
+}
+// Inverse: raw moments m1 = k1 + u k0, m2 = k2 + 2 u k1 + u^2 k0, then the
+// three-point inverse f(-1) = (m2 - m1)/2, f(0) = m0 - m2, f(1) = (m1 + m2)/2.
+template <typename T>
+__device__ __forceinline__ void bwd3(T& k0, T& k1, T& k2, T u) {
+  const T m1 = k1 + u * k0;
+  const T m2 = k2 + u * (k1 + m1);
+  const T fm = T(0.5) * (m2 - m1);
+  const T fz = k0 - m2;
+  const T fp = T(0.5) * (m1 + m2);
+  k0 = fm;
+  k1 = fz;
+  k2 = fp;
+}
+
+template <typename T>
+__device__ __forceinline__ void forward_cm(T (&f)[27], T ux, T uy, T uz) {
+#pragma unroll
+  for (int l = 0; l < 9; ++l) fwd3(f[3 * l], f[3 * l + 1], f[3 * l + 2], ux);
+#pragma unroll
+  for (int iz = 0; iz < 3; ++iz)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) fwd3(f[a + 9 * iz], f[a + 9 * iz + 3], f[a + 9 * iz + 6], uy);
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) fwd3(f[a + 3 * b], f[a + 3 * b + 9], f[a + 3 * b + 18], uz);
+}
+
+template <typename T>
+__device__ __forceinline__ void backward_cm(T (&k)[27], T ux, T uy, T uz) {
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) bwd3(k[a + 3 * b], k[a + 3 * b + 9], k[a + 3 * b + 18], uz);
+#pragma unroll
+  for (int iz = 0; iz < 3; ++iz)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) bwd3(k[a + 9 * iz], k[a + 9 * iz + 3], k[a + 9 * iz + 6], uy);
+#pragma unroll
+  for (int l = 0; l < 9; ++l) bwd3(k[3 * l], k[3 * l + 1], k[3 * l + 2], ux);
+}
+
+// ---- equilibrium central moments (Secs. III.A-III.D) ------------------------------
+
+template <typename T>
+__device__ __forceinline__ void keq_model(int model, T rho, T p, T ux, T uy, T uz, T (&e)[27]) {
+  const T cs2 = Lat<T>::CS2, cs4 = Lat<T>::CS4;
+  const T d = p - rho * cs2;
+  const T x2 = ux * ux, y2 = uy * uy, z2 = uz * uz;
+#pragma unroll
+  for (int r = 0; r < 27; ++r) e[r] = T(0);
+  e[KI(0, 0, 0)] = rho;
+  e[KI(2, 0, 0)] = e[KI(0, 2, 0)] = e[KI(0, 0, 2)] = p;
+  if (model == 3) {  // Model D: velocity independent
+    e[KI(2, 2, 0)] = e[KI(2, 0, 2)] = e[KI(0, 2, 2)] = p * cs2;
+    e[KI(2, 2, 2)] = p * cs4;
+  } else if (model == 2) {  // Model C
+    e[KI(2, 2, 0)] = p * cs2 - d * (x2 + y2);
+    e[KI(2, 0, 2)] = p * cs2 - d * (x2 + z2);
+    e[KI(0, 2, 2)] = p * cs2 - d * (y2 + z2);
+    e[KI(2, 1, 1)] = -d * uy * uz;
+    e[KI(1, 2, 1)] = -d * ux * uz;
+    e[KI(1, 1, 2)] = -d * ux * uy;
+    e[KI(1, 2, 2)] = d * ux * (T(2) * y2 + T(2) * z2 + cs2);
+    e[KI(2, 1, 2)] = d * uy * (T(2) * x2 + T(2) * z2 + cs2);
+    e[KI(2, 2, 1)] = d * uz * (T(2) * x2 + T(2) * y2 + cs2);
+    e[KI(2, 2, 2)] = p * cs4 - T(3) * d * (x2 * y2 + x2 * z2 + y2 * z2 + cs2 * (x2 + y2 + z2));
+  } else {  // Models A (0) and B (1) share the terms in (p - rho cs2)
+    e[KI(1, 2, 0)] = -d * ux;
+    e[KI(1, 0, 2)] = -d * ux;
+    e[KI(0, 1, 2)] = -d * uy;
+    e[KI(2, 1, 0)] = -d * uy;
+    e[KI(2, 0, 1)] = -d * uz;
+    e[KI(0, 2, 1)] = -d * uz;
+    e[KI(2, 2, 0)] = p * cs2 + d * (x2 + y2);
+    e[KI(2, 0, 2)] = p * cs2 + d * (x2 + z2);
+    e[KI(0, 2, 2)] = p * cs2 + d * (y2 + z2);
+    e[KI(2, 1, 1)] = d * uy * uz;
+    e[KI(1, 2, 1)] = d * ux * uz;
+    e[KI(1, 1, 2)] = d * ux * uy;
+    e[KI(1, 2, 2)] = -d * ux * (y2 + z2 + cs2);
+    e[KI(2, 1, 2)] = -d * uy * (x2 + z2 + cs2);
+    e[KI(2, 2, 1)] = -d * uz * (x2 + y2 + cs2);
+    e[KI(2, 2, 2)] = p * cs4 + d * (x2 * y2 + x2 * z2 + y2 * z2 + cs2 * (x2 + y2 + z2));
+    if (model == 0) {  // the extra rho u terms of Model A
+      e[KI(1, 2, 0)] -= rho * ux * y2;
+      e[KI(1, 0, 2)] -= rho * ux * z2;
+      e[KI(0, 1, 2)] -= rho * uy * z2;
+      e[KI(2, 1, 0)] -= rho * x2 * uy;
+      e[KI(2, 0, 1)] -= rho * x2 * uz;
+      e[KI(0, 2, 1)] -= rho * y2 * uz;
+      e[KI(1, 1, 1)] = -rho * ux * uy * uz;
+      e[KI(2, 2, 0)] += T(3) * rho * x2 * y2;
+      e[KI(2, 0, 2)] += T(3) * rho * x2 * z2;
+      e[KI(0, 2, 2)] += T(3) * rho * y2 * z2;
+      e[KI(2, 1, 1)] += T(3) * rho * x2 * uy * uz;
+      e[KI(1, 2, 1)] += T(3) * rho * ux * y2 * uz;
+      e[KI(1, 1, 2)] += T(3) * rho * ux * uy * z2;
+      e[KI(1, 2, 2)] -= rho * ux * (T(6) * y2 * z2 + cs2 * (y2 + z2));
+      e[KI(2, 1, 2)] -= rho * uy * (T(6) * x2 * z2 + cs2 * (x2 + z2));
+      e[KI(2, 2, 1)] -= rho * uz * (T(6) * x2 * y2 + cs2 * (x2 + y2));
+      e[KI(2, 2, 2)] += rho * (T(10) * x2 * y2 * z2 + T(3) * cs2 * (x2 * y2 + x2 * z2 + y2 * z2));
+    }
+  }
+}
+
+// ---- collision in central-moment space ----------------------------------------------
+// General form of Sec. II.B (any omega, any model), or the unit-rate Model D form
+// of Sec. III.E (all omega = 1 except omega_1) when UNIT is true.  On entry f
+// holds the pre-collision populations, on exit the post-collision ones.
+template <typename T, bool UNIT>
+__device__ __forceinline__ void collide_cm(T (&f)[27], T rho, T p, T ux, T uy, T uz,
+                                           const T (&F)[3], const T (&Q)[3], T om1,
+                                           const Phys<T>& ph) {
+  const T cs2 = Lat<T>::CS2, cs4 = Lat<T>::CS4;
+  forward_cm(f, ux, uy, uz);
+  T(&k)[27] = f;
+  if (UNIT) {
+    k[KI(1, 0, 0)] = F[0] / T(2);
+    k[KI(0, 1, 0)] = F[1] / T(2);
+    k[KI(0, 0, 1)] = F[2] / T(2);
+    k[KI(1, 1, 0)] = (T(1) - om1) * k[KI(1, 1, 0)];
+    k[KI(0, 1, 1)] = (T(1) - om1) * k[KI(0, 1, 1)];
+    k[KI(1, 0, 1)] = (T(1) - om1) * k[KI(1, 0, 1)];
+    const T h1 = T(1) - om1 / T(2);
+    const T d1 = (T(1) - om1) * (k[KI(2, 0, 0)] - k[KI(0, 2, 0)]) + h1 * (Q[0] - Q[1]);
+    const T d2 = (T(1) - om1) * (k[KI(2, 0, 0)] - k[KI(0, 0, 2)]) + h1 * (Q[0] - Q[2]);
+    const T tr = T(3) * p + (Q[0] + Q[1] + Q[2]) / T(2);
+    k[KI(2, 0, 0)] = (tr + d1 + d2) / T(3);
+    k[KI(0, 2, 0)] = (tr - T(2) * d1 + d2) / T(3);
+    k[KI(0, 0, 2)] = (tr + d1 - T(2) * d2) / T(3);
+    k[KI(1, 2, 0)] = k[KI(1, 0, 2)] = cs2 * F[0] / T(2);
+    k[KI(2, 1, 0)] = k[KI(0, 1, 2)] = cs2 * F[1] / T(2);
+    k[KI(2, 0, 1)] = k[KI(0, 2, 1)] = cs2 * F[2] / T(2);
+    k[KI(1, 1, 1)] = T(0);
+    k[KI(2, 2, 0)] = k[KI(2, 0, 2)] = k[KI(0, 2, 2)] = p * cs2;
+    k[KI(2, 1, 1)] = k[KI(1, 2, 1)] = k[KI(1, 1, 2)] = T(0);
+    k[KI(1, 2, 2)] = cs4 * F[0] / T(2);
+    k[KI(2, 1, 2)] = cs4 * F[1] / T(2);
+    k[KI(2, 2, 1)] = cs4 * F[2] / T(2);
+    k[KI(2, 2, 2)] = p * cs4;
+  } else {
+    T e[27];
+    keq_model(ph.model, rho, p, ux, uy, uz, e);
+    const T* om = ph.om;
+    const T o0 = om[0], o2 = om[2], o3 = om[3], o4 = om[4], o5 = om[5], o6 = om[6],
+            o7 = om[7], o8 = om[8], o9 = om[9], o10 = om[10];
+    // first order
+    k[KI(1, 0, 0)] = (T(1) - o0) * k[KI(1, 0, 0)] + (T(1) - o0 / T(2)) * F[0];
+    k[KI(0, 1, 0)] = (T(1) - o0) * k[KI(0, 1, 0)] + (T(1) - o0 / T(2)) * F[1];
+    k[KI(0, 0, 1)] = (T(1) - o0) * k[KI(0, 0, 1)] + (T(1) - o0 / T(2)) * F[2];
+    // second order
+    k[KI(1, 1, 0)] = (T(1) - om1) * k[KI(1, 1, 0)] + om1 * e[KI(1, 1, 0)];
+    k[KI(0, 1, 1)] = (T(1) - om1) * k[KI(0, 1, 1)] + om1 * e[KI(0, 1, 1)];
+    k[KI(1, 0, 1)] = (T(1) - om1) * k[KI(1, 0, 1)] + om1 * e[KI(1, 0, 1)];
+    {
+      const T a = k[KI(2, 0, 0)], b = k[KI(0, 2, 0)], c = k[KI(0, 0, 2)];
+      const T ea = e[KI(2, 0, 0)], eb = e[KI(0, 2, 0)], ec = e[KI(0, 0, 2)];
+      const T h1 = T(1) - om1 / T(2);
+      const T d1 = (T(1) - om1) * (a - b) + om1 * (ea - eb) + h1 * (Q[0] - Q[1]);
+      const T d2 = (T(1) - om1) * (a - c) + om1 * (ea - ec) + h1 * (Q[0] - Q[2]);
+      const T tr = (T(1) - o2) * (a + b + c) + o2 * (ea + eb + ec) +
+                   (T(1) - o2 / T(2)) * (Q[0] + Q[1] + Q[2]);
+      k[KI(2, 0, 0)] = (tr + d1 + d2) / T(3);
+      k[KI(0, 2, 0)] = (tr - T(2) * d1 + d2) / T(3);
+      k[KI(0, 0, 2)] = (tr + d1 - T(2) * d2) / T(3);
+    }
+    // third order: sums relax with omega_3 (with forcing), differences with omega_4
+    {
+      const int p1[3] = {KI(1, 2, 0), KI(2, 1, 0), KI(2, 0, 1)};
+      const int p2[3] = {KI(1, 0, 2), KI(0, 1, 2), KI(0, 2, 1)};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const T k1 = k[p1[a]], k2 = k[p2[a]], e1 = e[p1[a]], e2 = e[p2[a]];
+        const T s = (T(1) - o3) * (k1 + k2) + o3 * (e1 + e2) + T(2) * (T(1) - o3 / T(2)) * F[a] * cs2;
+        const T dd = (T(1) - o4) * (k1 - k2) + o4 * (e1 - e2);
+        k[p1[a]] = (s + dd) / T(2);
+        k[p2[a]] = (s - dd) / T(2);
+      }
+      k[KI(1, 1, 1)] = (T(1) - o5) * k[KI(1, 1, 1)] + o5 * e[KI(1, 1, 1)];
+    }
+    // fourth order
+    {
+      const T a = k[KI(2, 2, 0)], b = k[KI(2, 0, 2)], c = k[KI(0, 2, 2)];
+      const T ea = e[KI(2, 2, 0)], eb = e[KI(2, 0, 2)], ec = e[KI(0, 2, 2)];
+      const T A = (T(1) - o6) * (a - T(2) * b + c) + o6 * (ea - T(2) * eb + ec);
+      const T B = (T(1) - o6) * (a + b - T(2) * c) + o6 * (ea + eb - T(2) * ec);
+      const T C = (T(1) - o7) * (a + b + c) + o7 * (ea + eb + ec);
+      k[KI(2, 2, 0)] = (C + A + B) / T(3);
+      k[KI(2, 0, 2)] = (C - A) / T(3);
+      k[KI(0, 2, 2)] = (C - B) / T(3);
+    }
+    k[KI(2, 1, 1)] = (T(1) - o8) * k[KI(2, 1, 1)] + o8 * e[KI(2, 1, 1)];
+    k[KI(1, 2, 1)] = (T(1) - o8) * k[KI(1, 2, 1)] + o8 * e[KI(1, 2, 1)];
+    k[KI(1, 1, 2)] = (T(1) - o8) * k[KI(1, 1, 2)] + o8 * e[KI(1, 1, 2)];
+    // fifth order, with forcing
+    k[KI(1, 2, 2)] = (T(1) - o9) * k[KI(1, 2, 2)] + o9 * e[KI(1, 2, 2)] + (T(1) - o9 / T(2)) * F[0] * cs4;
+    k[KI(2, 1, 2)] = (T(1) - o9) * k[KI(2, 1, 2)] + o9 * e[KI(2, 1, 2)] + (T(1) - o9 / T(2)) * F[1] * cs4;
+    k[KI(2, 2, 1)] = (T(1) - o9) * k[KI(2, 2, 1)] + o9 * e[KI(2, 2, 1)] + (T(1) - o9 / T(2)) * F[2] * cs4;
+    // sixth order
+    k[KI(2, 2, 2)] = (T(1) - o10) * k[KI(2, 2, 2)] + o10 * e[KI(2, 2, 2)];
+  }
+  backward_cm(k, ux, uy, uz);
+}
+
+// ---- pass 1: streaming of both colours and the macroscopic sums ----------------------
+
+template <typename T, bool SOLID>
+__global__ void __launch_bounds__(128) k_macro(Geom g, Ptrs<T> P, Phys<T> ph) {
+  Cell c;
+  if (!make_cell(g, c)) return;
+  const long long S = g.stride;
+  const uint32_t mask = SOLID ? ld(P.mask + c.idx) : 0u;
+  T rr = T(0), rb = T(0), jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    const int src = nbr(c, -CX(q), -CY(q), -CZ(q));
+    T fr, fb, ft;
+    pull_colour<T, SOLID>(P, S, q, src, mask, fr, fb, ft);
+    rr += fr;
+    rb += fb;
+    if (CX(q) != 0) jx += T(CX(q)) * ft;
+    if (CY(q) != 0) jy += T(CY(q)) * ft;
+    if (CZ(q) != 0) jz += T(CZ(q)) * ft;
+  }
+  P.mac[c.idx] = rr;
+  P.mac[S + c.idx] = rb;
+  P.mac[2 * S + c.idx] = jx;
+  P.mac[3 * S + c.idx] = jy;
+  P.mac[4 * S + c.idx] = jz;
+  const bool self_solid = SOLID && ((mask >> SELF_SOLID_BIT) & 1u);
+  P.phi[c.idx] = self_solid ? T(0) : order_parameter(rr, rb, ph);
+  if (!isfinite(rr + rb)) atomicOr(P.flag, 1u);
+}
+
+// ---- pass 2: colour gradient (isotropic difference) and unit normal -------------------
+
+template <typename T, bool SOLID>
+__global__ void __launch_bounds__(128) k_normal(Geom g, Ptrs<T> P) {
+  Cell c;
+  if (!make_cell(g, c)) return;
+  const long long S = g.stride;
+  const uint32_t mask = SOLID ? ld(P.mask + c.idx) : 0u;
+  T gr[3] = {T(0), T(0), T(0)};
+  if (!(SOLID && ((mask >> SELF_SOLID_BIT) & 1u))) {
+    const T pc = P.phi[c.idx];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      if (q == REST) continue;
+      T v = ld(P.phi + nbr(c, CX(q), CY(q), CZ(q)));
+      if (SOLID && ((mask >> q) & 1u)) v = pc;
+      const T wv = WQ<T>(q) * v;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (CA(q, a) != 0) gr[a] += T(CA(q, a)) * wv;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) gr[a] /= Lat<T>::CS2;
+  }
+  const T g2 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+  const bool ok = g2 > T(1e-24);
+  const T len = ok ? sqrt(g2) : T(1);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    P.grad[a * S + c.idx] = gr[a];
+    P.nrm[a * S + c.idx] = ok ? gr[a] / len : T(0);
+  }
+}
+
+// ---- pass 3: curvature, forces, velocity and the recoloring state ------------------------
+
+template <typename T, bool SOLID>
+__global__ void __launch_bounds__(128) k_force(Geom g, Ptrs<T> P, Phys<T> ph) {
+  Cell c;
+  if (!make_cell(g, c)) return;
+  const long long S = g.stride;
+  const int i0 = c.idx;
+  const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
+  if (SOLID && ((mask >> SELF_SOLID_BIT) & 1u)) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      P.force[a * S + i0] = T(0);
+      P.wv[a * S + i0] = T(0);
+    }
+#pragma unroll
+    for (int a = 0; a < 5; ++a) P.s_out[a * S + i0] = T(0);
+    return;
+  }
+  const T nc[3] = {P.nrm[i0], P.nrm[S + i0], P.nrm[2 * S + i0]};
+  T dn[3][3];  // dn[a][b] = sum_i w_i n_b(x + c_i) c_ia
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) dn[a][b] = T(0);
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    if (q == REST) continue;
+    const int nb = nbr(c, CX(q), CY(q), CZ(q));
+    const bool use_c = SOLID && ((mask >> q) & 1u);
+    T nv[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) nv[b] = use_c ? nc[b] : ld(P.nrm + b * S + nb);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (CA(q, a) != 0)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) dn[a][b] += T(CA(q, a)) * (WQ<T>(q) * nv[b]);
+  }
+  T div = T(0), nnd = T(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    div += dn[a][a] / Lat<T>::CS2;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) nnd += nc[a] * nc[b] * dn[a][b] / Lat<T>::CS2;
+  }
+  const T kappa = -(div - nnd);
+  const T rr = P.mac[i0], rb = P.mac[S + i0];
+  const T rho = rr + rb;
+  const T p = rr * ph.cr2 + rb * ph.cb2;
+  T fbody[3] = {T(0), T(0), T(0)};
+  if (ph.force_mode == 1) {
+    for (int a = 0; a < 3; ++a) fbody[a] = ph.g[a];
+  } else if (ph.force_mode == 2) {
+    for (int a = 0; a < 3; ++a) fbody[a] = rho * ph.g[a];
+  } else if (ph.force_mode == 3) {
+    for (int a = 0; a < 3; ++a) fbody[a] = (rho - ph.rho_ref) * ph.g[a];
+  }
+  const T rfac = ph.beta * rr * rb / (rho * rho) * p;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const T Fa = T(0.5) * ph.sigma * kappa * P.grad[a * S + i0] + fbody[a];
+    const T ua = (P.mac[(2 + a) * S + i0] + Fa / T(2)) / rho;
+    P.force[a * S + i0] = Fa;
+    P.wv[a * S + i0] = (p - rho * Lat<T>::CS2) * ua;
+    P.s_out[(2 + a) * S + i0] = rfac * nc[a];
+  }
+  P.s_out[i0] = rr / rho;
+  P.s_out[S + i0] = rb / rho;
+}
+
+// ---- pass 4: streaming of the totals, correction term, collision --------------------------
+
+template <typename T, bool SOLID, bool UNIT>
+__global__ void __launch_bounds__(128) k_collide(Geom g, Ptrs<T> P, Phys<T> ph) {
+  Cell c;
+  if (!make_cell(g, c)) return;
+  const long long S = g.stride;
+  const int i0 = c.idx;
+  const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
+  if (SOLID && ((mask >> SELF_SOLID_BIT) & 1u)) {
+    // fullway bounce-back: keep what streamed in, reversed, colour by colour
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      const int src = nbr(c, -CX(q), -CY(q), -CZ(q));
+      T fr, fb, ft;
+      pull_colour<T, SOLID>(P, S, q, src, mask, fr, fb, ft);
+      P.f_out[OPP(q) * S + i0] = fr;
+      P.aux_out[OPP(q) * S + i0] = fb;
+    }
+    return;
+  }
+  T f[27];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    const int src = nbr(c, -CX(q), -CY(q), -CZ(q));
+    T v = ld(P.f_in + q * S + src);
+    if (SOLID && ((mask >> OPP(q)) & 1u)) v += ld(P.aux_in + q * S + src);
+    f[q] = v;
+  }
+  const T rr = P.mac[i0], rb = P.mac[S + i0];
+  const T rho = rr + rb;
+  const T p = rr * ph.cr2 + rb * ph.cb2;
+  const T phi = order_parameter(rr, rb, ph);
+  const T nu = T(0.5) * (T(1) + phi) * ph.nu_r + T(0.5) * (T(1) - phi) * ph.nu_b;
+  const T tau = T(0.5) + rho * nu / p;
+  const T om1 = T(1) / tau;
+  T j[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int q = 0; q < 27; ++q)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (CA(q, a) != 0) j[a] += T(CA(q, a)) * f[q];
+  const T F[3] = {P.force[i0], P.force[S + i0], P.force[2 * S + i0]};
+  T u[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u[a] = (j[a] + F[a] / T(2)) / rho;
+  T Q[3] = {T(0), T(0), T(0)};
+  if (ph.use_Q) {
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      if (q == REST) continue;
+      const int nb = nbr(c, CX(q), CY(q), CZ(q));
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (CA(q, a) != 0) Q[a] += T(CA(q, a)) * (WQ<T>(q) * ld(P.wv + a * S + nb));
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Q[a] = T(-3) * Q[a] / Lat<T>::CS2;
+  }
+  collide_cm<T, UNIT>(f, rho, p, u[0], u[1], u[2], F, Q, om1, ph);
+#pragma unroll
+  for (int q = 0; q < 27; ++q) P.f_out[q * S + i0] = f[q];
+}
+
+// ---- initialisation, read-back, reductions ------------------------------------------------
+
+// self-solid flags from the user mask and the bounce-back axes (in place, bytes)
+__global__ void k_solid_self(Geom g, uint8_t* solid, int has_user, int bx, int by, int bz);
+// neighbour mask from the self-solid flags
+__global__ void k_solid_mask(Geom g, const uint8_t* solid, uint32_t* mask);
+
+template <typename T, bool SOLID>
+__global__ void __launch_bounds__(128) k_init(Geom g, Ptrs<T> P, Phys<T> ph, const double* in_rr,
+                                              const double* in_rb, const double* in_u, long long n) {
+  Cell c;
+  if (!make_cell(g, c)) return;
+  const long long S = g.stride;
+  const int i0 = c.idx;
+  const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
+  if (SOLID && ((mask >> SELF_SOLID_BIT) & 1u)) {
+    for (int q = 0; q < 27; ++q) {
+      P.f_out[q * S + i0] = T(0);
+      P.aux_out[q * S + i0] = T(0);
+    }
+    for (int a = 0; a < 5; ++a) {
+      P.s_out[a * S + i0] = T(0);
+      P.mac[a * S + i0] = T(0);
+    }
+    for (int a = 0; a < 3; ++a) P.force[a * S + i0] = T(0);
+    P.phi[i0] = T(0);
+    return;
+  }
+  const T rr = T(in_rr[i0]), rb = T(in_rb[i0]);
+  const T u[3] = {T(in_u[i0]), T(in_u[n + i0]), T(in_u[2 * n + i0])};
+  const T rho = rr + rb;
+  const T p = rr * ph.cr2 + rb * ph.cb2;
+  T k[27];
+  keq_model(ph.model, rho, p, u[0], u[1], u[2], k);
+  backward_cm(k, u[0], u[1], u[2]);
+#pragma unroll
+  for (int q = 0; q < 27; ++q) P.f_out[q * S + i0] = k[q];
+  if (SOLID)
+    for (int q = 0; q < 27; ++q) P.aux_out[q * S + i0] = T(0);
+  P.s_out[i0] = rr / rho;
+  P.s_out[S + i0] = rb / rho;
+  P.s_out[2 * S + i0] = P.s_out[3 * S + i0] = P.s_out[4 * S + i0] = T(0);
+  P.mac[i0] = rr;
+  P.mac[S + i0] = rb;
+  for (int a = 0; a < 3; ++a) {
+    P.mac[(2 + a) * S + i0] = rho * u[a];
+    P.force[a * S + i0] = T(0);
+  }
+  P.phi[i0] = order_parameter(rr, rb, ph);
+}
+
+// macroscopic fields to FP64: [rho_r][rho_b][u 3][p][phi], each n long
+template <typename T, bool SOLID>
+__global__ void __launch_bounds__(128) k_read_macros(Geom g, Ptrs<T> P, Phys<T> ph, double* out,
+                                                     long long n) {
+  Cell c;
+  if (!make_cell(g, c)) return;
+  const long long S = g.stride;
+  const int i0 = c.idx;
+  const T rr = P.mac[i0], rb = P.mac[S + i0];
+  out[i0] = double(rr);
+  out[n + i0] = double(rb);
+  const bool solid = SOLID && ((ld(P.mask + i0) >> SELF_SOLID_BIT) & 1u);
+  if (solid) {
+    for (int a = 0; a < 5; ++a) out[(2 + a) * n + i0] = 0.0;
+    return;
+  }
+  const T rho = rr + rb;
+  for (int a = 0; a < 3; ++a)
+    out[(2 + a) * n + i0] = double((P.mac[(2 + a) * S + i0] + P.force[a * S + i0] / T(2)) / rho);
+  out[5 * n + i0] = double(rr * ph.cr2 + rb * ph.cb2);
+  out[6 * n + i0] = double(order_parameter(rr, rb, ph));
+}
+
+// two-colour post-collision populations of lattice direction q to FP64
+template <typename T, bool SOLID>
+__global__ void __launch_bounds__(128) k_read_pop(Geom g, Ptrs<T> P, int q, double* out_r,
+                                                  double* out_b) {
+  Cell c;
+  if (!make_cell(g, c)) return;
+  const long long S = g.stride;
+  const int i0 = c.idx;
+  const T f = P.f_in[q * S + i0];
+  const bool solid = SOLID && ((ld(P.mask + i0) >> SELF_SOLID_BIT) & 1u);
+  if (solid) {
+    out_r[i0] = double(f);
+    out_b[i0] = double(P.aux_in[q * S + i0]);
+    return;
+  }
+  const T cR = T(CX(q)) * P.s_in[2 * S + i0] + T(CY(q)) * P.s_in[3 * S + i0] +
+               T(CZ(q)) * P.s_in[4 * S + i0];
+  const T t = (q == REST) ? T(0) : (WQ<T>(q) / Lat<T>::CS2) * cR;
+  out_r[i0] = double(P.s_in[i0] * f + t);
+  out_b[i0] = double(P.s_in[S + i0] * f - t);
+}
+
+// FP64 block partial sums of rho_r and rho_b in a fixed order
+template <typename T>
+__global__ void __launch_bounds__(256) k_mass_partial(Geom g, const T* mac, long long n,
+                                                      double* partial) {
+  __shared__ double sr[256], sb[256];
+  const long long per_block = (n + gridDim.x - 1) / gridDim.x;
+  const long long lo = blockIdx.x * per_block;
+  const long long hi = min(n, lo + per_block);
+  double ar = 0.0, ab = 0.0;
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    ar += double(mac[i]);
+    ab += double(mac[g.stride + i]);
+  }
+  sr[threadIdx.x] = ar;
+  sb[threadIdx.x] = ab;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sr[threadIdx.x] += sr[threadIdx.x + s];
+      sb[threadIdx.x] += sb[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = sr[0];
+    partial[2 * blockIdx.x + 1] = sb[0];
+  }
+}
+
+__global__ void k_mass_final(const double* partial, int nblocks, double* out);
+
+}  // namespace cg27

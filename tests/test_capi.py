@@ -1,0 +1,90 @@
+"""The C-ABI library loads and exports every symbol include/cg27.h declares;
+host-side validation works without a GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "cg27.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(cg_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def cg():
+    from paper_2309_07801_gb300 import build, cg as binding
+    build.build()
+    binding.lib()
+    return binding
+
+
+def test_every_declared_symbol_is_exported(cg):
+    names = declared_functions()
+    assert len(names) >= 15
+    L = ctypes.CDLL(cg.LIB_PATH)
+    for n in names:
+        assert hasattr(L, n), n
+    # and the binding wraps each of them under the same name
+    assert set(names) == set(cg.SIGNATURES)
+
+
+def test_params_struct_layout_matches_header(cg):
+    # offsets follow the C declaration order; size includes the trailing ints
+    p = cg.cg_params()
+    assert ctypes.sizeof(p) == 4 * 6 + 8 * 8 + 8 * 11 + 8 * 3 + 8 + 4 * 6
+    assert cg.cg_abi_version() == 1
+
+
+def test_defaults_and_workspace(cg):
+    p = cg.cg_params_default(32, 16, 8)
+    assert (p.nx, p.ny, p.nz) == (32, 16, 8)
+    assert p.model == cg.CG_MODEL_D and p.use_Q == 1 and p.precision == cg.CG_F32
+    assert all(p.omega[q] == 1.0 for q in range(11))
+    assert abs(p.alpha_r - 8 / 27) < 1e-16 and p.beta == 0.7
+    n = 32 * 16 * 8
+    b32 = cg.cg_workspace_bytes(p)
+    # two population copies (27) + two recoloring states (5) + 18 side fields
+    assert b32 >= n * 4 * (2 * 27 + 2 * 5 + 18)
+    p.precision = cg.CG_F64
+    assert cg.cg_workspace_bytes(p) >= 2 * n * 4 * (2 * 27 + 2 * 5 + 18)
+    p.precision = cg.CG_F32
+    p.bc[2] = cg.CG_BC_BOUNCEBACK
+    assert cg.cg_workspace_bytes(p) > b32  # walls reserve the blue part and the mask
+
+
+@pytest.mark.parametrize("field,value", [("nx", 0), ("rho_r0", 0.0), ("alpha_b", 1.0),
+                                         ("nu_r", -1.0), ("model", 7), ("force_mode", 9),
+                                         ("precision", 5), ("reserved_", 1)])
+def test_invalid_params_rejected(cg, field, value):
+    p = cg.cg_params_default(8, 8, 8)
+    setattr(p, field, value)
+    with pytest.raises(cg.CGError) as e:
+        cg.cg_workspace_bytes(p)
+    assert e.value.code in (-1, -2)
+    assert cg.cg_last_error()
+
+
+def test_bounceback_axis_needs_three_cells(cg):
+    p = cg.cg_params_default(8, 8, 2)
+    p.bc[2] = cg.CG_BC_BOUNCEBACK
+    with pytest.raises(cg.CGError):
+        cg.cg_workspace_bytes(p)
+
+
+def test_create_rejects_bad_workspace(cg):
+    p = cg.cg_params_default(8, 8, 8)
+    need = cg.cg_workspace_bytes(p)
+    with pytest.raises(cg.CGError) as e:
+        cg.cg_create(p, 0, need, 0)
+    assert e.value.code == -5
+    with pytest.raises(cg.CGError) as e:
+        cg.cg_create(p, 256, need - 1, 0)
+    assert e.value.code == -5
+    with pytest.raises(cg.CGError) as e:
+        cg.cg_create(p, 257, need, 0)
+    assert e.value.code == -5

@@ -1,0 +1,264 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (normwise: max |gpu - oracle| / max |oracle| per field):
+  FP64 storage and arithmetic  <= 1e-12 on every macroscopic field and on both
+                                  colours' populations;
+  FP32 storage and arithmetic  total density <= 1e-5 relative in every cell,
+                                  velocity <= 1e-6 absolute (lattice units).
+Velocities are scaled by max(max|u|, 1e-3) so that a near-static flow is
+compared against a lattice velocity scale rather than round-off.
+"""
+import numpy as np
+import pytest
+
+from paper_2309_07801_gb300 import inputs
+from parity_util import compare_macros, compare_populations, run_pair, rel_err
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2309_07801_gb300 import build, cg
+    build.build()
+    cg.lib()
+    import oracle
+    oracle.build()
+
+
+def _assert_f64(od, gd, tol=F64_TOL):
+    m = compare_macros(od, gd)
+    f = compare_populations(od, gd)
+    bad = {k: v for k, v in {**m, **f}.items() if k not in ("u_abs", "rho_cellrel") and v > tol}
+    assert not bad, {**m, **f}
+
+
+def _ratio_params(nx, ny, nz, ratio=10.0, **kw):
+    ar, ab = inputs.rest_fractions(1.0, 1.0 / ratio)
+    d = dict(nx=nx, ny=ny, nz=nz, rho_r0=1.0, rho_b0=1.0 / ratio, alpha_r=ar, alpha_b=ab,
+             nu_r=0.05, nu_b=0.08, sigma=0.01, beta=0.7)
+    d.update(kw)
+    return d
+
+
+def _droplet(params, noise=1e-3, seed=1, u0=(0.02, -0.01, 0.015), R=None):
+    nx, ny, nz = params["nx"], params["ny"], params["nz"]
+    R = R if R is not None else min(nx, ny, nz) / 4.0
+    return inputs.droplet_fields((nz, ny, nx), (nx / 2 - 0.3, ny / 2 + 0.2, nz / 2 - 0.1), R,
+                                 params["rho_r0"], params["rho_b0"], u0=u0, noise=noise, seed=seed)
+
+
+# ---- FP64: the static-droplet workload (32^3, R=8) with noise, 200 steps ---------------
+
+def test_f64_static_droplet_32_200_steps():
+    wl = inputs.static_droplet_32()
+    fields = inputs.workload_fields(wl, noise=1e-3, seed=1)
+    od, gd = run_pair(wl.params(), fields, wl.steps, "f64")
+    _assert_f64(od, gd)
+    mo, _ = od.mass(), None
+    mg, flag = gd.mass()
+    assert flag == 0
+    assert np.all(np.abs(mg - mo) / mo < 1e-13)
+
+
+# ---- FP64: ragged sizes, density ratio, forces, models, relaxation rates ----------------
+
+@pytest.mark.parametrize("model", [0, 1, 2, 3])
+def test_f64_models_general_rates(model):
+    rng = np.random.default_rng(100 + model)
+    om = list(rng.uniform(0.8, 1.6, 11))
+    params = _ratio_params(13, 11, 9, model=model, omega=om, force_mode=2, g=(1e-5, -2e-5, -3e-5))
+    od, gd = run_pair(params, _droplet(params, seed=model), 40, "f64")
+    _assert_f64(od, gd)
+
+
+@pytest.mark.parametrize("model", [0, 2, 3])
+def test_f64_models_unit_rates(model):
+    params = _ratio_params(12, 10, 7, model=model, force_mode=1, g=(2e-5, 0.0, -1e-5))
+    od, gd = run_pair(params, _droplet(params, seed=7), 50, "f64")
+    _assert_f64(od, gd)
+
+
+def test_f64_without_correction_term():
+    params = _ratio_params(11, 9, 10, use_Q=0)
+    od, gd = run_pair(params, _droplet(params, seed=3), 40, "f64")
+    _assert_f64(od, gd)
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 1), (1, 0, 0), (0, 1, 1), (1, 1, 1)])
+def test_f64_bounceback_walls(bc):
+    params = _ratio_params(10, 9, 12, bc=bc, force_mode=3, g=(0.0, 0.0, -2e-5), rho_ref=1.0)
+    od, gd = run_pair(params, _droplet(params, seed=11), 60, "f64")
+    _assert_f64(od, gd)
+    assert np.all(np.abs(gd.mass()[0] - od.mass()) / od.mass() < 1e-13)
+
+
+def test_f64_solid_mask_obstacle_general_rates():
+    params = _ratio_params(14, 10, 9, bc=(0, 0, 1), omega=[1.2] * 11, force_mode=1,
+                           g=(3e-5, 0.0, 0.0))
+    solid = np.zeros((9, 10, 14), dtype=np.uint8)
+    solid[3:6, 2:5, 4:7] = 1          # a block obstacle
+    solid[5, 8, 11] = 1               # and an isolated solid cell
+    fields = _droplet(params, seed=5, R=2.5)
+    od, gd = run_pair(params, fields, 50, "f64", solid=solid)
+    _assert_f64(od, gd)
+
+
+def test_f64_layered_column():
+    """Pseudo-1D channel (nx = ny = 1): every x and y neighbour is the cell itself."""
+    rr0, rb0, ab = 0.1, 0.8, 0.9
+    params = dict(nx=1, ny=1, nz=40, bc=(0, 0, 1), rho_r0=rr0, rho_b0=rb0,
+                  alpha_r=1 - (1 - ab) / (rr0 / rb0), alpha_b=ab, nu_r=0.1, nu_b=0.1,
+                  sigma=0.002 / 4.5, force_mode=1, g=(1.5e-8, 0.0, 0.0))
+    od, gd = run_pair(params, inputs.layered_fields(40, 9.5, rr0, rb0), 400, "f64")
+    _assert_f64(od, gd)
+
+
+def test_f64_degenerate_sizes():
+    # one cell, one row, one plane; and a zero-step call
+    for shape in [(1, 1, 1), (7, 1, 1), (1, 5, 1), (4, 3, 1)]:
+        params = _ratio_params(*shape)
+        nx, ny, nz = shape
+        rr = np.full((nz, ny, nx), 0.6)
+        rb = np.full((nz, ny, nx), 0.04)
+        u = np.zeros((3, nz, ny, nx))
+        u[0] = 0.03
+        od, gd = run_pair(params, (rr, rb, u), 5, "f64")
+        _assert_f64(od, gd)
+        gd.step(0)
+        _assert_f64(od, gd)
+
+
+def test_initial_state_matches():
+    params = _ratio_params(9, 8, 7)
+    od, gd = run_pair(params, _droplet(params, seed=2), 0, "f64")
+    _assert_f64(od, gd)
+
+
+# ---- FP32 ------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("noise", [0.0, 1e-3])
+def test_f32_static_droplet_32_200_steps(noise):
+    wl = inputs.static_droplet_32()
+    fields = inputs.workload_fields(wl, noise=noise, seed=1)
+    od, gd = run_pair(wl.params(), fields, wl.steps, "f32")
+    m = compare_macros(od, gd)
+    assert m["rho_cellrel"] <= 1e-5, m
+    assert m["u_abs"] <= 1e-6, m
+
+
+def test_f32_translating_droplet_ratio10_32_200_steps():
+    wl = inputs.translating_droplet(32)
+    fields = inputs.workload_fields(wl)
+    od, gd = run_pair(wl.params(), fields, 200, "f32")
+    m = compare_macros(od, gd)
+    assert m["rho_cellrel"] <= 1e-5, m
+    assert m["u_abs"] <= 1e-6, m
+
+
+def test_f32_walls_and_gravity():
+    params = _ratio_params(16, 12, 20, bc=(0, 0, 1), force_mode=3, g=(0.0, 0.0, -1e-5), rho_ref=1.0)
+    od, gd = run_pair(params, _droplet(params, seed=9), 200, "f32")
+    m = compare_macros(od, gd)
+    assert m["rho_cellrel"] <= 1e-5, m
+    assert m["u_abs"] <= 1e-6, m
+
+
+# ---- the benchmark workload at full size (128^3, ratio 10, FP32) -------------------------
+
+def test_f32_translating_droplet_128_full_size():
+    """The exact domain and launch configuration the benchmark times, checked
+    against the oracle over its first steps on every cell."""
+    wl = inputs.translating_droplet(128)
+    fields = inputs.workload_fields(wl)
+    od, gd = run_pair(wl.params(), fields, 2, "f32")
+    m = compare_macros(od, gd)
+    assert m["rho_cellrel"] <= 1e-6, m
+    assert m["u_abs"] <= 1e-7, m
+
+
+def test_f32_full_size_conservation_and_translation():
+    """At full size: per-colour mass conserved over 100 steps, and a periodic
+    shift of the input shifts the output bit for bit."""
+    from paper_2309_07801_gb300 import cg
+    wl = inputs.translating_droplet(128)
+    rr, rb, u = inputs.workload_fields(wl)
+    p = cg.make_params(precision="f32", **wl.params())
+    outs = []
+    for s in ((0, 0, 0), (17, -5, 33)):
+        d = cg.Domain(p)
+        d.init(np.roll(rr, s, (0, 1, 2)), np.roll(rb, s, (0, 1, 2)), np.roll(u, s, (1, 2, 3)))
+        m0, _ = d.mass()
+        d.step(100)
+        m1, flag = d.mass()
+        assert flag == 0
+        assert np.all(np.abs(m1 - m0) / m0 < 2e-6), (m0, m1)
+        outs.append(d.macros())
+        d.close()
+    for key in ("rho_r", "rho_b", "p", "phi"):
+        assert np.array_equal(np.roll(outs[0][key], (17, -5, 33), (0, 1, 2)), outs[1][key])
+    assert np.array_equal(np.roll(outs[0]["u"], (17, -5, 33), (1, 2, 3)), outs[1]["u"])
+
+
+# ---- checkpoint, determinism, failure detection ---------------------------------------
+
+def test_checkpoint_resume_is_bitwise():
+    from paper_2309_07801_gb300 import cg
+    params = _ratio_params(16, 12, 10, bc=(0, 0, 1))
+    fields = _droplet(params, seed=4)
+    for prec in ("f64", "f32"):
+        p = cg.make_params(precision=prec, **params)
+        a = cg.Domain(p)
+        a.init(*fields)
+        a.step(7)
+        blob = a.save()
+        a.step(9)
+        ref = a.populations()
+        b = cg.Domain(p)
+        b.load(blob)
+        assert b.steps == 7
+        b.step(9)
+        got = b.populations()
+        assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1])
+        # the same run repeated gives the same bits (no atomics on the hot path)
+        c = cg.Domain(p)
+        c.init(*fields)
+        c.step(16)
+        again = c.populations()
+        assert np.array_equal(ref[0], again[0]) and np.array_equal(ref[1], again[1])
+
+
+def test_nonfinite_is_flagged():
+    """A run driven unstable (nu = 0 and a huge force) sets the non-finite flag;
+    nothing faults and the context stays usable."""
+    from paper_2309_07801_gb300 import cg
+    params = _ratio_params(8, 8, 8, nu_r=0.0, nu_b=0.0, force_mode=1, g=(0.5, 0.5, 0.5))
+    d = cg.Domain(cg.make_params(precision="f32", **params))
+    d.init(*_droplet(params, seed=1))
+    d.step(200)
+    _, flag = d.mass()
+    assert flag == 1
+    ok = cg.Domain(cg.make_params(precision="f32", **_ratio_params(8, 8, 8)))
+    ok.init(*_droplet(_ratio_params(8, 8, 8), seed=1))
+    ok.step(3)
+    assert ok.mass()[1] == 0
+
+
+def test_invalid_inputs_rejected_before_launch():
+    from paper_2309_07801_gb300 import cg
+    params = _ratio_params(6, 6, 6)
+    d = cg.Domain(cg.make_params(precision="f32", **params))
+    rr, rb, u = _droplet(params)
+    rr = rr.copy()
+    rr[0, 0, 0] = np.nan
+    with pytest.raises(cg.CGError):
+        d.init(rr, rb, u)
+    with pytest.raises(cg.CGError):
+        d.step(1)  # not initialised
+    with pytest.raises(cg.CGError):
+        d.init(*_droplet(params), solid=np.zeros((6, 6, 6), np.uint8))  # no wall workspace

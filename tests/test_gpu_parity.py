@@ -178,8 +178,8 @@ def test_f32_translating_droplet_128_full_size():
     fields = inputs.workload_fields(wl)
     od, gd = run_pair(wl.params(), fields, 2, "f32")
     m = compare_macros(od, gd)
-    assert m["rho_cellrel"] <= 1e-6, m
-    assert m["u_abs"] <= 1e-7, m
+    assert m["rho_cellrel"] <= 1e-5, m
+    assert m["u_abs"] <= 1e-6, m
 
 
 def test_f32_full_size_conservation_and_translation():

@@ -163,6 +163,27 @@ int cg_steps_taken(cg_ctx *ctx, int64_t *steps);
 int cg_profile_enable(cg_ctx *ctx, int64_t max_steps);
 int cg_profile_read(cg_ctx *ctx, double ms[CG_NUM_PASSES], int64_t *steps);
 
+/* Per-colour mass of two device density fields, without any allocation.
+ * The paper has no counterpart: this is a service of the library.  It is for
+ * callers that cannot allocate device memory where they need the sums -- code
+ * that only holds device pointers to density fields and owns no domain
+ * workspace, or code running where cudaMalloc is not allowed (it may
+ * synchronise the whole device, or another allocator already reserves all
+ * device memory).  d_rho_r, d_rho_b: n values each on the current device, FP32
+ * or FP64 as `precision` says; out_mass (host): sum of rho_r and of rho_b,
+ * accumulated in FP64 in a fixed order (same values as cg_reduce() up to
+ * summation order).  The block partial sums live in a 64 KiB file-scope
+ * __device__ array that every GPU loading the library holds until the process
+ * exits.  The first call on a device looks up that array's device address
+ * (make it before any stream capture).  Every call overwrites the slots it
+ * reads, so nothing has to start at zero, but all calls share the one array:
+ * calls that overlap on the GPU (other streams, other host threads) race.
+ * n above CG_NOALLOC_MAX_CELLS is rejected with CG_ERR_INVALID_ARG before any
+ * launch.  Enqueued on cuda_stream, which it synchronises before returning. */
+#define CG_NOALLOC_MAX_CELLS 67108864
+int cg_mass_noalloc(const void *d_rho_r, const void *d_rho_b, int64_t n,
+                    int32_t precision, void *cuda_stream, double out_mass[2]);
+
 /* Release the domain (the workspace stays the caller's). */
 int cg_destroy(cg_ctx *ctx);
 

@@ -63,6 +63,7 @@ SIGNATURES = {
     "cg_steps_taken": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     "cg_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "cg_profile_read": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_int64)]),
+    "cg_mass_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_int32, _VP, _VP]),
     "cg_destroy": (ctypes.c_int, [_VP]),
     "cg_last_error": (ctypes.c_char_p, []),
     "cg_abi_version": (ctypes.c_int, []),
@@ -179,6 +180,17 @@ def cg_profile_read(h):
 
 
 PASS_NAMES = ("k_macro", "k_normal", "k_force", "k_collide")
+
+CG_NOALLOC_MAX_CELLS = 67108864
+
+
+def cg_mass_noalloc(d_rho_r: int, d_rho_b: int, n: int, precision: int, stream: int) -> np.ndarray:
+    """Per-colour mass of two device density fields (device pointers), using the
+    library's static scratch instead of a workspace."""
+    out = np.zeros(2)
+    _check(lib().cg_mass_noalloc(ctypes.c_void_p(d_rho_r), ctypes.c_void_p(d_rho_b), int(n),
+                                 int(precision), ctypes.c_void_p(stream), _ptr(out)))
+    return out
 
 
 def cg_destroy(h):

@@ -299,6 +299,11 @@ __global__ void k_mass_final(const double* partial, int nblocks, double* out) {
 }
 }  // namespace cg27
 
+// error recording shared with the other translation units of the library
+__attribute__((visibility("hidden"))) int cg27_internal_fail(int code, const char* msg) {
+  return fail(code, msg);
+}
+
 // ---- C ABI --------------------------------------------------------------------------
 
 extern "C" {

@@ -34,7 +34,7 @@ if ROOT not in sys.path:
 METRIC = "D3Q27 CG-CM MLUPS"
 UNIT = "MLUPS"
 STEP_BYTES_432 = 432          # paper layout: 2 colours x 27 FP32 populations, read + write
-COLLIDE_BYTES_PER_CELL = 248  # k_collide: F in (108) + rho_r, rho_b (8) + F (12) + (p-rho cs2)u (12) + F out (108)
+COLLIDE_BYTES_PER_CELL = 248  # k_collide: f in (108) + rho_r, rho_b (8) + F (12) + Q (12) + f out (108)
 
 
 def parse_args():
@@ -299,13 +299,14 @@ def run_ours(args, dist):
     value = N * K * dist.world / (ms_total * 1e-3) / 1e6
 
     peak, peak_kind = load_peaks()
-    collide_ms = pass_ms[3] / max(1, timed)
+    collide_ms = pass_ms[cg.PASS_NAMES.index("k_collide")] / max(1, timed)
     achieved = COLLIDE_BYTES_PER_CELL * N / (collide_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak,
                 "traffic": recorded_traffic("k_collide", N),
                 "peak_kind": peak_kind, "bytes_per_cell": COLLIDE_BYTES_PER_CELL,
-                "pass_ms_per_step": {cg.PASS_NAMES[i]: pass_ms[i] / max(1, timed) for i in range(4)}}
+                "pass_ms_per_step": {cg.PASS_NAMES[i]: pass_ms[i] / max(1, timed)
+                                     for i in range(len(cg.PASS_NAMES))}}
     step_roofline = {"bytes_per_cell": STEP_BYTES_432,
                      "frac": value / dist.world * 1e6 * STEP_BYTES_432 / (peak * 1e9),
                      "peak": peak, "unit": "GB/s"}
@@ -344,7 +345,7 @@ def run_ours(args, dist):
                        "l2": "inputs larger than L2: population state 2 x %.0f MB" %
                              (N * 128 / 1e6)},
             "roofline": roofline, "step_roofline_432B": step_roofline,
-            "e2e": e2e, "gpu_launches": 4 * K, "clocks": clk,
+            "e2e": e2e, "gpu_launches": len(cg.PASS_NAMES) * K, "clocks": clk,
             "mass": list(map(float, mass)), "nonfinite": nonfinite}
     if not args.no_cpu_baseline and dist.world == 1:
         line["cpu_baseline"] = cpu_baseline(args.edge, args.cpu_budget)

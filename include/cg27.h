@@ -154,11 +154,12 @@ int cg_load_state(cg_ctx *ctx, const void *host, size_t bytes);
 int cg_steps_taken(cg_ctx *ctx, int64_t *steps);
 
 /* Per-pass device timing.  cg_profile_enable(ctx, max_steps) makes the next
- * max_steps calls of the step loop record CUDA events around each of its four
+ * max_steps calls of the step loop record CUDA events around each of its
  * passes (max_steps = 0 turns timing off).  cg_profile_read() synchronises the
- * stream and returns, for passes 0..3 (streaming + sums, colour gradient,
- * force/recoloring state, streaming + collision), the summed device time in
- * milliseconds and the number of timed steps. */
+ * stream and returns, for passes 0..CG_NUM_PASSES-1 (streaming of both colours
+ * and sums; gradient, normal, curvature, forces and recoloring state;
+ * correction term; streaming of the totals and collision), the summed device
+ * time in milliseconds and the number of timed steps. */
 #define CG_NUM_PASSES 4
 int cg_profile_enable(cg_ctx *ctx, int64_t max_steps);
 int cg_profile_read(cg_ctx *ctx, double ms[CG_NUM_PASSES], int64_t *steps);

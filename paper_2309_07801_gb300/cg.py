@@ -172,14 +172,17 @@ def cg_profile_enable(h, max_steps: int):
     _check(lib().cg_profile_enable(h, int(max_steps)))
 
 
+CG_NUM_PASSES = 4
+
+
 def cg_profile_read(h):
-    ms = np.zeros(4)
+    ms = np.zeros(CG_NUM_PASSES)
     n = ctypes.c_int64(0)
     _check(lib().cg_profile_read(h, _ptr(ms), ctypes.byref(n)))
     return ms, n.value
 
 
-PASS_NAMES = ("k_macro", "k_normal", "k_force", "k_collide")
+PASS_NAMES = ("k_macro", "k_fields", "k_qcorr", "k_collide")
 
 CG_NOALLOC_MAX_CELLS = 67108864
 

@@ -3,6 +3,7 @@
 // read-back, reductions and checkpoints.  Device code is in cg27_device.cuh.
 #include "cg27.h"
 #include "cg27_device.cuh"
+#include "cg27_step.cuh"
 
 #include <cmath>
 #include <cstdio>
@@ -42,6 +43,7 @@ int paper_to_lex(int i) {
 }
 
 constexpr int RED_THREADS = 256;
+constexpr int NUM_EVENTS_PER_STEP = CG_NUM_PASSES + 1;
 
 struct Layout {
   long long n = 0, stride = 0;
@@ -49,7 +51,7 @@ struct Layout {
   bool solid = false;
   int red_blocks = 0;
   size_t f[2] = {0, 0}, s[2] = {0, 0}, aux[2] = {0, 0};
-  size_t mask = 0, mac = 0, phi = 0, grad = 0, nrm = 0, force = 0, wv = 0;
+  size_t mask = 0, mac = 0, phi = 0, qc = 0, force = 0, wv = 0;
   size_t partial = 0, flag = 0, result = 0, total = 0;
 };
 
@@ -109,8 +111,7 @@ Layout make_layout(const cg_params& p) {
   }
   L.mac = take(5 * field);
   L.phi = take(field);
-  L.grad = take(3 * field);
-  L.nrm = take(3 * field);
+  L.qc = take(3 * field);
   L.force = take(3 * field);
   L.wv = take(3 * field);
   L.partial = take((size_t)L.red_blocks * 2 * sizeof(double));
@@ -135,7 +136,9 @@ struct cg_ctx {
   int64_t steps = 0;
   bool initialised = false;
   bool unit = false;  // all omega = 1 except omega_1, Model D: the Sec. III.E form
-  // per-pass timing: events[5 * s + k] brackets pass k of timed step s
+  int tz = 1;         // z planes per tile of the step kernels
+  int collide_blocks = 0;  // persistent grid of k_collide (set on first launch)
+  // per-pass timing: events[NUM_EVENTS_PER_STEP * s + k] brackets pass k of timed step s
   std::vector<cudaEvent_t> events;
   int64_t prof_capacity = 0, prof_used = 0;
   ~cg_ctx() {
@@ -151,6 +154,8 @@ Phys<T> make_phys(const cg_params& p) {
   const double xi = 9.0 / 19.0;
   ph.rho_r0 = T(p.rho_r0);
   ph.rho_b0 = T(p.rho_b0);
+  ph.inv_rho_r0 = T(1.0 / p.rho_r0);
+  ph.inv_rho_b0 = T(1.0 / p.rho_b0);
   ph.cr2 = T(xi * (1.0 - p.alpha_r));
   ph.cb2 = T(xi * (1.0 - p.alpha_b));
   ph.nu_r = T(p.nu_r);
@@ -195,34 +200,56 @@ Ptrs<T> make_ptrs(const cg_ctx* c, int cur) {
   P.mask = L.solid ? reinterpret_cast<const uint32_t*>(w + L.mask) : nullptr;
   P.mac = reinterpret_cast<T*>(w + L.mac);
   P.phi = reinterpret_cast<T*>(w + L.phi);
-  P.grad = reinterpret_cast<T*>(w + L.grad);
-  P.nrm = reinterpret_cast<T*>(w + L.nrm);
+  P.qc = reinterpret_cast<T*>(w + L.qc);
   P.force = reinterpret_cast<T*>(w + L.force);
   P.wv = reinterpret_cast<T*>(w + L.wv);
   P.flag = reinterpret_cast<unsigned int*>(w + L.flag);
   return P;
 }
 
+// persistent grid of k_collide: every SM filled to its occupancy
+template <typename T, bool SOLID, bool UNIT>
+int collide_blocks(const cg_ctx* c) {
+  int dev = 0, sms = 148, per_sm = 1;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_collide<T, SOLID, UNIT>,
+                                                    CollideCfg<T>::CT, 0) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const int xt = (c->prm.nx + CollideCfg<T>::CT - 1) / CollideCfg<T>::CT;
+  const long long items = (long long)xt * c->prm.ny * c->prm.nz;
+  return (int)std::min<long long>(items, (long long)sms * per_sm);
+}
+
+template <typename T, bool SOLID, bool UNIT>
+void launch_collide(cg_ctx* c, const Geom& g, const Ptrs<T>& P, const Phys<T>& ph) {
+  if (c->collide_blocks <= 0) c->collide_blocks = collide_blocks<T, SOLID, UNIT>(c);
+  const int xt = (c->prm.nx + CollideCfg<T>::CT - 1) / CollideCfg<T>::CT;
+  const long long items = (long long)xt * c->prm.ny * c->prm.nz;
+  k_collide<T, SOLID, UNIT><<<c->collide_blocks, CollideCfg<T>::CT, 0, c->stream>>>(g, P, ph, xt, items);
+}
+
 template <typename T, bool SOLID>
 void enqueue_step(cg_ctx* c) {
   const int cur = (int)(c->steps & 1);
   const Geom g = make_geom(c);
-  const dim3 b = block_of(c->prm), gr = grid_of(c->prm, b);
+  const dim3 b(TX, TY, 1);
+  const dim3 gr((c->prm.nx + TX - 1) / TX, (c->prm.ny + TY - 1) / TY, (c->prm.nz + c->tz - 1) / c->tz);
+  const dim3 bc = block_of(c->prm), gc = grid_of(c->prm, bc);
   const Ptrs<T> P = make_ptrs<T>(c, cur);
   const Phys<T> ph = make_phys<T>(c->prm);
   cudaEvent_t* ev = nullptr;
-  if (c->prof_used < c->prof_capacity) ev = &c->events[5 * c->prof_used++];
+  if (c->prof_used < c->prof_capacity) ev = &c->events[NUM_EVENTS_PER_STEP * c->prof_used++];
   if (ev) cudaEventRecord(ev[0], c->stream);
-  k_macro<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph);
+  k_macro<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph, c->tz);
   if (ev) cudaEventRecord(ev[1], c->stream);
-  k_normal<T, SOLID><<<gr, b, 0, c->stream>>>(g, P);
+  k_fields<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph, c->tz);
   if (ev) cudaEventRecord(ev[2], c->stream);
-  k_force<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph);
+  if (c->prm.use_Q) k_qcorr<T><<<gc, bc, 0, c->stream>>>(g, P);
   if (ev) cudaEventRecord(ev[3], c->stream);
   if (c->unit)
-    k_collide<T, SOLID, true><<<gr, b, 0, c->stream>>>(g, P, ph);
+    launch_collide<T, SOLID, true>(c, g, P, ph);
   else
-    k_collide<T, SOLID, false><<<gr, b, 0, c->stream>>>(g, P, ph);
+    launch_collide<T, SOLID, false>(c, g, P, ph);
   if (ev) cudaEventRecord(ev[4], c->stream);
 }
 
@@ -363,6 +390,13 @@ int cg_create(const cg_params* p, void* d_workspace, size_t bytes, void* cuda_st
   for (int q = 0; q < 11; ++q)
     if (q != 1 && p->omega[q] != 1.0) unit = false;
   c->unit = unit;
+  // z planes per tile: enough tiles for about eight per SM
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long tiles_xy = (long long)((p->nx + TX - 1) / TX) * ((p->ny + TY - 1) / TY);
+  const long long chunks = std::max(1LL, std::min<long long>(p->nz, (8LL * sms + tiles_xy - 1) / tiles_xy));
+  c->tz = (int)((p->nz + chunks - 1) / chunks);
   *out = c;
   return CG_OK;
 }
@@ -516,7 +550,7 @@ int cg_profile_enable(cg_ctx* c, int64_t max_steps) {
   if (!c) return fail(CG_ERR_INVALID_ARG, "ctx is NULL");
   if (max_steps < 0 || max_steps > (1 << 20)) return fail(CG_ERR_INVALID_ARG, "max_steps out of range");
   CG_CUDA(cudaStreamSynchronize(c->stream));
-  while ((int64_t)c->events.size() < 5 * max_steps) {
+  while ((int64_t)c->events.size() < NUM_EVENTS_PER_STEP * max_steps) {
     cudaEvent_t e;
     CG_CUDA(cudaEventCreate(&e));
     c->events.push_back(e);
@@ -529,11 +563,12 @@ int cg_profile_enable(cg_ctx* c, int64_t max_steps) {
 int cg_profile_read(cg_ctx* c, double ms[CG_NUM_PASSES], int64_t* steps) {
   if (!c) return fail(CG_ERR_INVALID_ARG, "ctx is NULL");
   CG_CUDA(cudaStreamSynchronize(c->stream));
-  double acc[CG_NUM_PASSES] = {0, 0, 0, 0};
+  double acc[CG_NUM_PASSES] = {0};
   for (int64_t s = 0; s < c->prof_used; ++s)
     for (int k = 0; k < CG_NUM_PASSES; ++k) {
       float t = 0.f;
-      CG_CUDA(cudaEventElapsedTime(&t, c->events[5 * s + k], c->events[5 * s + k + 1]));
+      CG_CUDA(cudaEventElapsedTime(&t, c->events[NUM_EVENTS_PER_STEP * s + k],
+                                   c->events[NUM_EVENTS_PER_STEP * s + k + 1]));
       acc[k] += t;
     }
   if (ms)

@@ -15,18 +15,16 @@
 //   MASK    per cell: bit q set when the neighbour x + c_q is solid, bit 27
 //           when the cell itself is solid (only with walls);
 //   MAC[5]  rho_r, rho_b, j_x, j_y, j_z of the post-streaming state;
-//   PHI     order parameter; GRAD[3], NRM[3] colour gradient and unit normal;
-//   FORCE[3] total force; WV[3] (p - rho c_s^2) u for the correction term.
+//   PHI     order parameter; FORCE[3] total force; WV[3] (p - rho c_s^2) u;
+//   QC[3]   correction term Q.
 // Lattice directions are stored in the lexicographic order
 // q = (c_x+1) + 3 (c_y+1) + 9 (c_z+1); moments use r = a + 3 b + 9 c.
 //
-// One step is four passes (each a kernel over all cells):
-//   k_macro   pull-stream the two colours, sum densities and momentum;
-//   k_normal  isotropic gradient of phi and the unit normal;
-//   k_force   curvature, CSF + body force, velocity, (p - rho c_s^2) u,
-//             recoloring vector R and fractions for the next state;
-//   k_collide pull-stream the totals, correction term Q, CM-MRT collision,
-//             store f^* (recoloring is applied by the next pull).
+// One step is four kernels (cg27_step.cuh): k_macro (pull both colours and
+// sum), k_fields (colour gradient, normal, curvature, forces, velocity,
+// (p - rho c_s^2) u, recoloring state), k_qcorr (correction term Q) and
+// k_collide (pull the totals, CM-MRT collision, store f^*; recoloring is
+// applied by the next pull).
 #pragma once
 
 #include <cstdint>
@@ -77,8 +75,7 @@ struct Ptrs {
   const uint32_t* mask;
   T* mac;
   T* phi;
-  T* grad;
-  T* nrm;
+  T* qc;  // correction term Q
   T* force;
   T* wv;
   unsigned int* flag;
@@ -87,6 +84,7 @@ struct Ptrs {
 template <typename T>
 struct Phys {
   T rho_r0, rho_b0;
+  T inv_rho_r0, inv_rho_b0;
   T cr2, cb2;  // (c_s^k)^2 = xi (1 - alpha_k)
   T nu_r, nu_b;
   T sigma, beta;
@@ -161,7 +159,7 @@ __device__ __forceinline__ void pull_colour(const Ptrs<T>& P, long long stride, 
 
 template <typename T>
 __device__ __forceinline__ T order_parameter(T rr, T rb, const Phys<T>& ph) {
-  const T a = rr / ph.rho_r0, b = rb / ph.rho_b0;
+  const T a = rr * ph.inv_rho_r0, b = rb * ph.inv_rho_b0;
   return (a + b > T(0)) ? (a - b) / (a + b) : T(0);
 }
 
@@ -293,6 +291,7 @@ __device__ __forceinline__ void collide_cm(T (&f)[27], T rho, T p, T ux, T uy, T
                                            const T (&F)[3], const T (&Q)[3], T om1,
                                            const Phys<T>& ph) {
   const T cs2 = Lat<T>::CS2, cs4 = Lat<T>::CS4;
+  const T third = T(1) / T(3);
   forward_cm(f, ux, uy, uz);
   T(&k)[27] = f;
   if (UNIT) {
@@ -306,9 +305,9 @@ __device__ __forceinline__ void collide_cm(T (&f)[27], T rho, T p, T ux, T uy, T
     const T d1 = (T(1) - om1) * (k[KI(2, 0, 0)] - k[KI(0, 2, 0)]) + h1 * (Q[0] - Q[1]);
     const T d2 = (T(1) - om1) * (k[KI(2, 0, 0)] - k[KI(0, 0, 2)]) + h1 * (Q[0] - Q[2]);
     const T tr = T(3) * p + (Q[0] + Q[1] + Q[2]) / T(2);
-    k[KI(2, 0, 0)] = (tr + d1 + d2) / T(3);
-    k[KI(0, 2, 0)] = (tr - T(2) * d1 + d2) / T(3);
-    k[KI(0, 0, 2)] = (tr + d1 - T(2) * d2) / T(3);
+    k[KI(2, 0, 0)] = (tr + d1 + d2) * third;
+    k[KI(0, 2, 0)] = (tr - T(2) * d1 + d2) * third;
+    k[KI(0, 0, 2)] = (tr + d1 - T(2) * d2) * third;
     k[KI(1, 2, 0)] = k[KI(1, 0, 2)] = cs2 * F[0] / T(2);
     k[KI(2, 1, 0)] = k[KI(0, 1, 2)] = cs2 * F[1] / T(2);
     k[KI(2, 0, 1)] = k[KI(0, 2, 1)] = cs2 * F[2] / T(2);
@@ -341,9 +340,9 @@ __device__ __forceinline__ void collide_cm(T (&f)[27], T rho, T p, T ux, T uy, T
       const T d2 = (T(1) - om1) * (a - c) + om1 * (ea - ec) + h1 * (Q[0] - Q[2]);
       const T tr = (T(1) - o2) * (a + b + c) + o2 * (ea + eb + ec) +
                    (T(1) - o2 / T(2)) * (Q[0] + Q[1] + Q[2]);
-      k[KI(2, 0, 0)] = (tr + d1 + d2) / T(3);
-      k[KI(0, 2, 0)] = (tr - T(2) * d1 + d2) / T(3);
-      k[KI(0, 0, 2)] = (tr + d1 - T(2) * d2) / T(3);
+      k[KI(2, 0, 0)] = (tr + d1 + d2) * third;
+      k[KI(0, 2, 0)] = (tr - T(2) * d1 + d2) * third;
+      k[KI(0, 0, 2)] = (tr + d1 - T(2) * d2) * third;
     }
     // third order: sums relax with omega_3 (with forcing), differences with omega_4
     {
@@ -366,9 +365,9 @@ __device__ __forceinline__ void collide_cm(T (&f)[27], T rho, T p, T ux, T uy, T
       const T A = (T(1) - o6) * (a - T(2) * b + c) + o6 * (ea - T(2) * eb + ec);
       const T B = (T(1) - o6) * (a + b - T(2) * c) + o6 * (ea + eb - T(2) * ec);
       const T C = (T(1) - o7) * (a + b + c) + o7 * (ea + eb + ec);
-      k[KI(2, 2, 0)] = (C + A + B) / T(3);
-      k[KI(2, 0, 2)] = (C - A) / T(3);
-      k[KI(0, 2, 2)] = (C - B) / T(3);
+      k[KI(2, 2, 0)] = (C + A + B) * third;
+      k[KI(2, 0, 2)] = (C - A) * third;
+      k[KI(0, 2, 2)] = (C - B) * third;
     }
     k[KI(2, 1, 1)] = (T(1) - o8) * k[KI(2, 1, 1)] + o8 * e[KI(2, 1, 1)];
     k[KI(1, 2, 1)] = (T(1) - o8) * k[KI(1, 2, 1)] + o8 * e[KI(1, 2, 1)];
@@ -381,205 +380,6 @@ __device__ __forceinline__ void collide_cm(T (&f)[27], T rho, T p, T ux, T uy, T
     k[KI(2, 2, 2)] = (T(1) - o10) * k[KI(2, 2, 2)] + o10 * e[KI(2, 2, 2)];
   }
   backward_cm(k, ux, uy, uz);
-}
-
-// ---- pass 1: streaming of both colours and the macroscopic sums ----------------------
-
-template <typename T, bool SOLID>
-__global__ void __launch_bounds__(128) k_macro(Geom g, Ptrs<T> P, Phys<T> ph) {
-  Cell c;
-  if (!make_cell(g, c)) return;
-  const long long S = g.stride;
-  const uint32_t mask = SOLID ? ld(P.mask + c.idx) : 0u;
-  T rr = T(0), rb = T(0), jx = T(0), jy = T(0), jz = T(0);
-#pragma unroll
-  for (int q = 0; q < 27; ++q) {
-    const int src = nbr(c, -CX(q), -CY(q), -CZ(q));
-    T fr, fb, ft;
-    pull_colour<T, SOLID>(P, S, q, src, mask, fr, fb, ft);
-    rr += fr;
-    rb += fb;
-    if (CX(q) != 0) jx += T(CX(q)) * ft;
-    if (CY(q) != 0) jy += T(CY(q)) * ft;
-    if (CZ(q) != 0) jz += T(CZ(q)) * ft;
-  }
-  P.mac[c.idx] = rr;
-  P.mac[S + c.idx] = rb;
-  P.mac[2 * S + c.idx] = jx;
-  P.mac[3 * S + c.idx] = jy;
-  P.mac[4 * S + c.idx] = jz;
-  const bool self_solid = SOLID && ((mask >> SELF_SOLID_BIT) & 1u);
-  P.phi[c.idx] = self_solid ? T(0) : order_parameter(rr, rb, ph);
-  if (!isfinite(rr + rb)) atomicOr(P.flag, 1u);
-}
-
-// ---- pass 2: colour gradient (isotropic difference) and unit normal -------------------
-
-template <typename T, bool SOLID>
-__global__ void __launch_bounds__(128) k_normal(Geom g, Ptrs<T> P) {
-  Cell c;
-  if (!make_cell(g, c)) return;
-  const long long S = g.stride;
-  const uint32_t mask = SOLID ? ld(P.mask + c.idx) : 0u;
-  T gr[3] = {T(0), T(0), T(0)};
-  if (!(SOLID && ((mask >> SELF_SOLID_BIT) & 1u))) {
-    const T pc = P.phi[c.idx];
-#pragma unroll
-    for (int q = 0; q < 27; ++q) {
-      if (q == REST) continue;
-      T v = ld(P.phi + nbr(c, CX(q), CY(q), CZ(q)));
-      if (SOLID && ((mask >> q) & 1u)) v = pc;
-      const T wv = WQ<T>(q) * v;
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-        if (CA(q, a) != 0) gr[a] += T(CA(q, a)) * wv;
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) gr[a] /= Lat<T>::CS2;
-  }
-  const T g2 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
-  const bool ok = g2 > T(1e-24);
-  const T len = ok ? sqrt(g2) : T(1);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    P.grad[a * S + c.idx] = gr[a];
-    P.nrm[a * S + c.idx] = ok ? gr[a] / len : T(0);
-  }
-}
-
-// ---- pass 3: curvature, forces, velocity and the recoloring state ------------------------
-
-template <typename T, bool SOLID>
-__global__ void __launch_bounds__(128) k_force(Geom g, Ptrs<T> P, Phys<T> ph) {
-  Cell c;
-  if (!make_cell(g, c)) return;
-  const long long S = g.stride;
-  const int i0 = c.idx;
-  const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
-  if (SOLID && ((mask >> SELF_SOLID_BIT) & 1u)) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      P.force[a * S + i0] = T(0);
-      P.wv[a * S + i0] = T(0);
-    }
-#pragma unroll
-    for (int a = 0; a < 5; ++a) P.s_out[a * S + i0] = T(0);
-    return;
-  }
-  const T nc[3] = {P.nrm[i0], P.nrm[S + i0], P.nrm[2 * S + i0]};
-  T dn[3][3];  // dn[a][b] = sum_i w_i n_b(x + c_i) c_ia
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) dn[a][b] = T(0);
-#pragma unroll
-  for (int q = 0; q < 27; ++q) {
-    if (q == REST) continue;
-    const int nb = nbr(c, CX(q), CY(q), CZ(q));
-    const bool use_c = SOLID && ((mask >> q) & 1u);
-    T nv[3];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) nv[b] = use_c ? nc[b] : ld(P.nrm + b * S + nb);
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-      if (CA(q, a) != 0)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) dn[a][b] += T(CA(q, a)) * (WQ<T>(q) * nv[b]);
-  }
-  T div = T(0), nnd = T(0);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    div += dn[a][a] / Lat<T>::CS2;
-#pragma unroll
-    for (int b = 0; b < 3; ++b) nnd += nc[a] * nc[b] * dn[a][b] / Lat<T>::CS2;
-  }
-  const T kappa = -(div - nnd);
-  const T rr = P.mac[i0], rb = P.mac[S + i0];
-  const T rho = rr + rb;
-  const T p = rr * ph.cr2 + rb * ph.cb2;
-  T fbody[3] = {T(0), T(0), T(0)};
-  if (ph.force_mode == 1) {
-    for (int a = 0; a < 3; ++a) fbody[a] = ph.g[a];
-  } else if (ph.force_mode == 2) {
-    for (int a = 0; a < 3; ++a) fbody[a] = rho * ph.g[a];
-  } else if (ph.force_mode == 3) {
-    for (int a = 0; a < 3; ++a) fbody[a] = (rho - ph.rho_ref) * ph.g[a];
-  }
-  const T rfac = ph.beta * rr * rb / (rho * rho) * p;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const T Fa = T(0.5) * ph.sigma * kappa * P.grad[a * S + i0] + fbody[a];
-    const T ua = (P.mac[(2 + a) * S + i0] + Fa / T(2)) / rho;
-    P.force[a * S + i0] = Fa;
-    P.wv[a * S + i0] = (p - rho * Lat<T>::CS2) * ua;
-    P.s_out[(2 + a) * S + i0] = rfac * nc[a];
-  }
-  P.s_out[i0] = rr / rho;
-  P.s_out[S + i0] = rb / rho;
-}
-
-// ---- pass 4: streaming of the totals, correction term, collision --------------------------
-
-template <typename T, bool SOLID, bool UNIT>
-__global__ void __launch_bounds__(128) k_collide(Geom g, Ptrs<T> P, Phys<T> ph) {
-  Cell c;
-  if (!make_cell(g, c)) return;
-  const long long S = g.stride;
-  const int i0 = c.idx;
-  const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
-  if (SOLID && ((mask >> SELF_SOLID_BIT) & 1u)) {
-    // fullway bounce-back: keep what streamed in, reversed, colour by colour
-#pragma unroll
-    for (int q = 0; q < 27; ++q) {
-      const int src = nbr(c, -CX(q), -CY(q), -CZ(q));
-      T fr, fb, ft;
-      pull_colour<T, SOLID>(P, S, q, src, mask, fr, fb, ft);
-      P.f_out[OPP(q) * S + i0] = fr;
-      P.aux_out[OPP(q) * S + i0] = fb;
-    }
-    return;
-  }
-  T f[27];
-#pragma unroll
-  for (int q = 0; q < 27; ++q) {
-    const int src = nbr(c, -CX(q), -CY(q), -CZ(q));
-    T v = ld(P.f_in + q * S + src);
-    if (SOLID && ((mask >> OPP(q)) & 1u)) v += ld(P.aux_in + q * S + src);
-    f[q] = v;
-  }
-  const T rr = P.mac[i0], rb = P.mac[S + i0];
-  const T rho = rr + rb;
-  const T p = rr * ph.cr2 + rb * ph.cb2;
-  const T phi = order_parameter(rr, rb, ph);
-  const T nu = T(0.5) * (T(1) + phi) * ph.nu_r + T(0.5) * (T(1) - phi) * ph.nu_b;
-  const T tau = T(0.5) + rho * nu / p;
-  const T om1 = T(1) / tau;
-  T j[3] = {T(0), T(0), T(0)};
-#pragma unroll
-  for (int q = 0; q < 27; ++q)
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-      if (CA(q, a) != 0) j[a] += T(CA(q, a)) * f[q];
-  const T F[3] = {P.force[i0], P.force[S + i0], P.force[2 * S + i0]};
-  T u[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) u[a] = (j[a] + F[a] / T(2)) / rho;
-  T Q[3] = {T(0), T(0), T(0)};
-  if (ph.use_Q) {
-#pragma unroll
-    for (int q = 0; q < 27; ++q) {
-      if (q == REST) continue;
-      const int nb = nbr(c, CX(q), CY(q), CZ(q));
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-        if (CA(q, a) != 0) Q[a] += T(CA(q, a)) * (WQ<T>(q) * ld(P.wv + a * S + nb));
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) Q[a] = T(-3) * Q[a] / Lat<T>::CS2;
-  }
-  collide_cm<T, UNIT>(f, rho, p, u[0], u[1], u[2], F, Q, om1, ph);
-#pragma unroll
-  for (int q = 0; q < 27; ++q) P.f_out[q * S + i0] = f[q];
 }
 
 // ---- initialisation, read-back, reductions ------------------------------------------------

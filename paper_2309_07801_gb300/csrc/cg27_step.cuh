@@ -1,0 +1,518 @@
+// cg27_step.cuh -- the three kernels of one time step, as z-marching tiles.
+//
+// k_macro and k_fields run one thread per (x, y) column of a TX x TY tile and
+// walk a range of z planes.  Neighbour data that a stencil reads from the planes
+// z-1, z, z+1 is staged in shared memory as a ring of planes (each plane loaded
+// once per tile, with its x-y halo and periodic wrap applied at load time), so a
+// neighbour read is one shared-memory load at a constant offset.  Populations
+// (pulled once per cell) come straight from global memory, all 27 loads issued
+// before they are used.
+//
+//   k_macro   pull both colours, sums rho_r, rho_b, j and phi        (Sec. II.A)
+//   k_fields  grad phi and n on the tile plus a 1-cell halo, then
+//             kappa, F, u, (p - rho c_s^2) u, R and the recoloring
+//             fractions on the tile                            (Secs. II.A, III.E)
+//   k_qcorr   correction term Q from (p - rho c_s^2) u             (Sec. III.E)
+//   k_collide persistent, cp.async-pipelined: pull the totals, CM-MRT
+//             collision, store f^*                          (Secs. II.B, III.E)
+#pragma once
+
+#include "cg27_device.cuh"
+
+namespace cg27 {
+
+constexpr int TX = 32, TY = 8, NT = TX * TY;
+
+__device__ __forceinline__ int wrapi(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+// this thread's column and its wrapped x / y neighbours
+struct Col {
+  int tx, ty, tid;
+  int x0, y0;  // tile origin
+  bool active;
+  int xs[3];   // x-1, x, x+1 (wrapped)
+  int ys[3];   // (y-1, y, y+1) * nx (wrapped)
+};
+
+__device__ __forceinline__ Col make_col(const Geom& g) {
+  Col c;
+  c.tx = threadIdx.x;
+  c.ty = threadIdx.y;
+  c.tid = c.tx + TX * c.ty;
+  c.x0 = blockIdx.x * TX;
+  c.y0 = blockIdx.y * TY;
+  const int x = c.x0 + c.tx, y = c.y0 + c.ty;
+  c.active = x < g.nx && y < g.ny;
+  const int xx = c.active ? x : 0, yy = c.active ? y : 0;
+  c.xs[0] = xx == 0 ? g.nx - 1 : xx - 1;
+  c.xs[1] = xx;
+  c.xs[2] = xx == g.nx - 1 ? 0 : xx + 1;
+  c.ys[0] = (yy == 0 ? g.ny - 1 : yy - 1) * g.nx;
+  c.ys[1] = yy * g.nx;
+  c.ys[2] = (yy == g.ny - 1 ? 0 : yy + 1) * g.nx;
+  return c;
+}
+
+__device__ __forceinline__ int ring3(int z) { return (z + 3) % 3; }
+
+// Positions of a plane's tile-plus-halo region that this thread loads: at most
+// two per thread for the regions used here; `xy` is the wrapped in-plane cell
+// offset (x + nx y) of each, -1 when unused.  Computed once per block.
+template <int HALO>
+struct HaloSlots {
+  static constexpr int W = TX + 2 * HALO, PL = W * (TY + 2 * HALO);
+  static constexpr int K = (PL + NT - 1) / NT;
+  int xy[K];
+  __device__ __forceinline__ void init(const Geom& g, const Col& c) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int i = c.tid + k * NT;
+      xy[k] = -1;
+      if (i < PL) {
+        const int lx = i % W, ly = i / W;
+        xy[k] = wrapi(c.x0 + lx - HALO, g.nx) + wrapi(c.y0 + ly - HALO, g.ny) * g.nx;
+      }
+    }
+  }
+};
+
+__device__ __forceinline__ int zoff(const Geom& g, int z) { return wrapi(z, g.nz) * g.nxy; }
+
+// ---- pass 1 -----------------------------------------------------------------------------
+
+template <typename T, bool SOLID>
+__global__ void __launch_bounds__(NT) k_macro(Geom g, Ptrs<T> P, Phys<T> ph, int tz) {
+  using HS = HaloSlots<1>;
+  constexpr int W = HS::W, PL = HS::PL;
+  // recoloring state of the planes z-1..z+1 (plus the one being prefetched when
+  // FP32 leaves room for a fourth slot), 1-cell halo
+  constexpr int RING = sizeof(T) == 4 ? 4 : 3;
+  __shared__ T sS[RING][5][PL];
+  const Col c = make_col(g);
+  const int z0 = blockIdx.z * tz, z1 = min(g.nz, z0 + tz);
+  const long long S = g.stride;
+  HS hs;
+  hs.init(g, c);
+  T pre[HS::K][5];
+  auto fetch = [&](int z) {
+    const int zo = zoff(g, z);
+#pragma unroll
+    for (int k = 0; k < HS::K; ++k)
+      if (hs.xy[k] >= 0)
+#pragma unroll
+        for (int f = 0; f < 5; ++f) pre[k][f] = ld(P.s_in + f * S + hs.xy[k] + zo);
+  };
+  auto store = [&](int z) {
+#pragma unroll
+    for (int k = 0; k < HS::K; ++k)
+      if (hs.xy[k] >= 0)
+#pragma unroll
+        for (int f = 0; f < 5; ++f) sS[(z + RING) % RING][f][c.tid + k * NT] = pre[k][f];
+  };
+  fetch(z0 - 1);
+  store(z0 - 1);
+  fetch(z0);
+  store(z0);
+  fetch(z0 + 1);
+  store(z0 + 1);
+  __syncthreads();
+  for (int z = z0; z < z1; ++z) {
+    fetch(z + 2);  // in flight while this plane is computed
+    if (c.active) {
+      const int zo[3] = {(z == 0 ? g.nz - 1 : z - 1) * g.nxy, z * g.nxy,
+                         (z == g.nz - 1 ? 0 : z + 1) * g.nxy};
+      const int i0 = c.xs[1] + c.ys[1] + zo[1];
+      const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
+      T f[27];
+#pragma unroll
+      for (int q = 0; q < 27; ++q)
+        f[q] = ld(P.f_in + q * S + (c.xs[1 - CX(q)] + c.ys[1 - CY(q)] + zo[1 - CZ(q)]));
+      T rr = T(0), rb = T(0), jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+      for (int q = 0; q < 27; ++q) {
+        const int src = c.xs[1 - CX(q)] + c.ys[1 - CY(q)] + zo[1 - CZ(q)];
+        T fr, fb, ft = f[q];
+        if (SOLID && ((mask >> OPP(q)) & 1u)) {
+          fr = f[q];
+          fb = ld(P.aux_in + q * S + src);
+          ft = fr + fb;
+        } else {
+          const T* s = &sS[(z - CZ(q) + RING) % RING][0][(c.tx + 1 - CX(q)) + W * (c.ty + 1 - CY(q))];
+          T t = T(0);
+          if (q != REST) {
+            T cR = T(0);
+            if (CX(q) != 0) cR += T(CX(q)) * s[2 * PL];
+            if (CY(q) != 0) cR += T(CY(q)) * s[3 * PL];
+            if (CZ(q) != 0) cR += T(CZ(q)) * s[4 * PL];
+            t = (WQ<T>(q) / Lat<T>::CS2) * cR;
+          }
+          fr = s[0] * f[q] + t;
+          fb = s[PL] * f[q] - t;
+        }
+        rr += fr;
+        rb += fb;
+        if (CX(q) != 0) jx += T(CX(q)) * ft;
+        if (CY(q) != 0) jy += T(CY(q)) * ft;
+        if (CZ(q) != 0) jz += T(CZ(q)) * ft;
+      }
+      P.mac[i0] = rr;
+      P.mac[S + i0] = rb;
+      P.mac[2 * S + i0] = jx;
+      P.mac[3 * S + i0] = jy;
+      P.mac[4 * S + i0] = jz;
+      const bool self_solid = SOLID && ((mask >> SELF_SOLID_BIT) & 1u);
+      P.phi[i0] = self_solid ? T(0) : order_parameter(rr, rb, ph);
+      if (!isfinite(rr + rb)) atomicOr(P.flag, 1u);
+    }
+    // with four slots plane z+2 goes to the slot of z-2, last read in the
+    // previous iteration; with three it replaces z-1, read by this one
+    if (RING == 3) __syncthreads();
+    store(z + 2);
+    __syncthreads();
+  }
+}
+
+// ---- pass 2 -----------------------------------------------------------------------------
+
+template <typename T, bool SOLID>
+__global__ void __launch_bounds__(NT) k_fields(Geom g, Ptrs<T> P, Phys<T> ph, int tz) {
+  using H2 = HaloSlots<2>;  // phi, 2-cell halo
+  using H1 = HaloSlots<1>;  // n, 1-cell halo
+  constexpr int W2 = H2::W, P2 = H2::PL, W1 = H1::W, P1 = H1::PL;
+  __shared__ T sPhi[3][P2];  // phi of three planes (ring3)
+  __shared__ T sN[3][3][P1];  // n of three planes (ring3)
+  __shared__ T sG[2][3][NT];  // grad phi of the tile cells, planes of parity 0 and 1
+  const Col c = make_col(g);
+  const int z0 = blockIdx.z * tz, z1 = min(g.nz, z0 + tz);
+  const long long S = g.stride;
+  H2 h2;
+  h2.init(g, c);
+  H1 h1;
+  h1.init(g, c);
+  T pphi[H2::K];
+  auto fetch_phi = [&](int z) {
+    const int zo = zoff(g, z);
+#pragma unroll
+    for (int k = 0; k < H2::K; ++k)
+      if (h2.xy[k] >= 0) pphi[k] = ld(P.phi + h2.xy[k] + zo);
+  };
+  auto store_phi = [&](int z) {
+#pragma unroll
+    for (int k = 0; k < H2::K; ++k)
+      if (h2.xy[k] >= 0) sPhi[ring3(z)][c.tid + k * NT] = pphi[k];
+  };
+
+  // grad phi and n of plane p on the tile plus a 1-cell halo (phi of p-1..p+1 staged)
+  auto normals = [&](int p) {
+    const int zo = zoff(g, p);
+#pragma unroll
+    for (int k = 0; k < H1::K; ++k) {
+      if (h1.xy[k] < 0) continue;
+      const int i = c.tid + k * NT;
+      const int lx = i % W1, ly = i / W1;
+      T gr[3] = {T(0), T(0), T(0)};
+      uint32_t mask = 0u;
+      bool self_solid = false;
+      if (SOLID) {
+        mask = ld(P.mask + h1.xy[k] + zo);
+        self_solid = (mask >> SELF_SOLID_BIT) & 1u;
+      }
+      if (!self_solid) {
+        const int ctr = (lx + 1) + W2 * (ly + 1);
+        const T pc = sPhi[ring3(p)][ctr];
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+          if (q == REST) continue;
+          T v = sPhi[ring3(p + CZ(q))][ctr + CX(q) + W2 * CY(q)];
+          if (SOLID && ((mask >> q) & 1u)) v = pc;
+          const T wv = WQ<T>(q) * v;
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+            if (CA(q, a) != 0) gr[a] += T(CA(q, a)) * wv;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gr[a] *= T(3);  // 1 / c_s^2
+      }
+      const T g2 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+      const bool ok = g2 > T(1e-24);
+      const T inv_len = ok ? T(1) / sqrt(g2) : T(0);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) sN[ring3(p)][a][i] = gr[a] * inv_len;
+      const int ix = lx - 1, iy = ly - 1;
+      if (ix >= 0 && ix < TX && iy >= 0 && iy < TY)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sG[p & 1][a][ix + TX * iy] = gr[a];
+    }
+  };
+
+  // prologue: phi of z0-2 .. z0+2 and n of z0-1, z0 (three-slot rings)
+  for (int p = z0 - 2; p <= z0; ++p) {
+    fetch_phi(p);
+    store_phi(p);
+  }
+  __syncthreads();
+  normals(z0 - 1);
+  fetch_phi(z0 + 1);
+  __syncthreads();
+  store_phi(z0 + 1);  // replaces z0-2
+  __syncthreads();
+  normals(z0);
+  fetch_phi(z0 + 2);
+  __syncthreads();
+  store_phi(z0 + 2);  // replaces z0-1
+  __syncthreads();
+
+  T mac[5];
+  auto fetch_mac = [&](int z) {
+    if (!c.active) return;
+    const int i0 = c.xs[1] + c.ys[1] + zoff(g, z);
+#pragma unroll
+    for (int f = 0; f < 5; ++f) mac[f] = ld(P.mac + f * S + i0);
+  };
+  fetch_mac(z0);
+  for (int z = z0; z < z1; ++z) {
+    fetch_phi(z + 3);  // in flight during this plane
+    normals(z + 1);
+    __syncthreads();
+    if (c.active) {
+      const int i0 = c.xs[1] + c.ys[1] + z * g.nxy;
+      const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
+      if (SOLID && ((mask >> SELF_SOLID_BIT) & 1u)) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          P.force[a * S + i0] = T(0);
+          P.wv[a * S + i0] = T(0);
+        }
+#pragma unroll
+        for (int a = 0; a < 5; ++a) P.s_out[a * S + i0] = T(0);
+      } else {
+        const int ctr = (c.tx + 1) + W1 * (c.ty + 1);
+        const T nc[3] = {sN[ring3(z)][0][ctr], sN[ring3(z)][1][ctr], sN[ring3(z)][2][ctr]};
+        T dn[3][3];  // dn[a][b] = sum_i w_i n_b(x + c_i) c_ia
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) dn[a][b] = T(0);
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+          if (q == REST) continue;
+          const bool use_c = SOLID && ((mask >> q) & 1u);
+          const int off = ctr + CX(q) + W1 * CY(q);
+          T nv[3];
+#pragma unroll
+          for (int b = 0; b < 3; ++b) nv[b] = use_c ? nc[b] : sN[ring3(z + CZ(q))][b][off];
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+            if (CA(q, a) != 0)
+#pragma unroll
+              for (int b = 0; b < 3; ++b) dn[a][b] += T(CA(q, a)) * (WQ<T>(q) * nv[b]);
+        }
+        T div = T(0), nnd = T(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          div += dn[a][a];
+#pragma unroll
+          for (int b = 0; b < 3; ++b) nnd += nc[a] * nc[b] * dn[a][b];
+        }
+        const T kappa = -T(3) * (div - nnd);  // derivatives carry 1 / c_s^2
+        const T rr = mac[0], rb = mac[1];
+        const T rho = rr + rb;
+        const T p = rr * ph.cr2 + rb * ph.cb2;
+        T fbody[3] = {T(0), T(0), T(0)};
+        if (ph.force_mode == 1) {
+          for (int a = 0; a < 3; ++a) fbody[a] = ph.g[a];
+        } else if (ph.force_mode == 2) {
+          for (int a = 0; a < 3; ++a) fbody[a] = rho * ph.g[a];
+        } else if (ph.force_mode == 3) {
+          for (int a = 0; a < 3; ++a) fbody[a] = (rho - ph.rho_ref) * ph.g[a];
+        }
+        const T inv_rho = T(1) / rho;
+        const T rfac = ph.beta * rr * rb * inv_rho * inv_rho * p;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const T Fa = T(0.5) * ph.sigma * kappa * sG[z & 1][a][c.tid] + fbody[a];
+          const T ua = (mac[2 + a] + T(0.5) * Fa) * inv_rho;
+          P.force[a * S + i0] = Fa;
+          P.wv[a * S + i0] = (p - rho * Lat<T>::CS2) * ua;
+          P.s_out[(2 + a) * S + i0] = rfac * nc[a];
+        }
+        P.s_out[i0] = rr * inv_rho;
+        P.s_out[S + i0] = rb * inv_rho;
+      }
+    }
+    fetch_mac(z + 1);
+    // phi of z+3 replaces z, last read by normals(z+1) before the barrier above
+    store_phi(z + 3);
+    __syncthreads();
+  }
+}
+
+// ---- pass 3: correction term ----------------------------------------------------------
+// Q_a = -3 d_a[(p - rho c_s^2) u_a] with d_a = (1/c_s^2) sum_i w_i c_ia (.)
+// (Sec. III.E); one thread per cell, neighbours through L1.
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_qcorr(Geom g, Ptrs<T> P) {
+  Cell c;
+  if (!make_cell(g, c)) return;
+  const long long S = g.stride;
+  T Q[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    if (q == REST) continue;
+    const int nb = nbr(c, CX(q), CY(q), CZ(q));
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (CA(q, a) != 0) Q[a] += T(CA(q, a)) * (WQ<T>(q) * ld(P.wv + a * S + nb));
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) P.qc[a * S + c.idx] = T(-9) * Q[a];
+}
+
+// ---- pass 4: streaming of the totals and the collision ----------------------------------
+// A persistent kernel: each thread walks cells (rows of CT cells along x) with a
+// stride of the whole grid.  While it computes one cell, the 35 values of its
+// next cell (27 pulled populations, rho_r, rho_b, F, Q) are already being
+// copied by cp.async into this thread's own shared-memory slots, so memory
+// latency is hidden without holding the loads in registers and without any
+// barrier (no thread reads another thread's slots).
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename T>
+struct CollideCfg {
+  static constexpr int CT = sizeof(T) == 4 ? 128 : 64;  // threads per block
+  static constexpr int NV = 35;                          // values staged per cell
+};
+
+// neighbour offsets of cell (x, y, z)
+__device__ __forceinline__ void cell_at(const Geom& g, int x, int y, int z, Cell& c) {
+  c.xs[0] = (x == 0 ? g.nx - 1 : x - 1);
+  c.xs[1] = x;
+  c.xs[2] = (x == g.nx - 1 ? 0 : x + 1);
+  c.ys[0] = (y == 0 ? g.ny - 1 : y - 1) * g.nx;
+  c.ys[1] = y * g.nx;
+  c.ys[2] = (y == g.ny - 1 ? 0 : y + 1) * g.nx;
+  c.zs[0] = (z == 0 ? g.nz - 1 : z - 1) * g.nxy;
+  c.zs[1] = z * g.nxy;
+  c.zs[2] = (z == g.nz - 1 ? 0 : z + 1) * g.nxy;
+  c.idx = x + c.ys[1] + c.zs[1];
+}
+
+template <typename T, bool SOLID, bool UNIT>
+__global__ void __launch_bounds__(CollideCfg<T>::CT) k_collide(Geom g, Ptrs<T> P, Phys<T> ph,
+                                                               int xtiles, long long nitems) {
+  constexpr int CT = CollideCfg<T>::CT, NV = CollideCfg<T>::NV;
+  __shared__ T buf[2][NV][CT];
+  const int t = threadIdx.x;
+  const long long S = g.stride;
+
+  // start the copies of work item `it` into stage `st`; returns the cell index
+  // (or -1 when this thread has no cell in the item)
+  auto issue = [&](long long it, int st) -> int {
+    const int xt = (int)(it % xtiles);
+    const long long r = it / xtiles;
+    const int y = (int)(r % g.ny), z = (int)(r / g.ny);
+    const int x = xt * CT + t;
+    if (x >= g.nx) return -1;
+    Cell c;
+    cell_at(g, x, y, z, c);
+#pragma unroll
+    for (int q = 0; q < 27; ++q)
+      cp_async_elem(&buf[st][q][t], P.f_in + q * S + nbr(c, -CX(q), -CY(q), -CZ(q)));
+    cp_async_elem(&buf[st][27][t], P.mac + c.idx);
+    cp_async_elem(&buf[st][28][t], P.mac + S + c.idx);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) cp_async_elem(&buf[st][29 + a][t], P.force + a * S + c.idx);
+    if (ph.use_Q) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) cp_async_elem(&buf[st][32 + a][t], P.qc + a * S + c.idx);
+    }
+    return c.idx;
+  };
+
+  long long it = blockIdx.x;
+  int st = 0;
+  int cur = it < nitems ? issue(it, 0) : -1;
+  cp_async_commit();
+  for (; it < nitems; it += gridDim.x) {
+    const long long nx_it = it + gridDim.x;
+    const int nxt = nx_it < nitems ? issue(nx_it, st ^ 1) : -1;
+    cp_async_commit();
+    cp_async_wait_one();  // the group of item `it` has landed
+    if (cur >= 0) {
+      const int i0 = cur;
+      uint32_t mask = 0u;
+      Cell c;
+      if (SOLID) {
+        mask = ld(P.mask + i0);
+        cell_at(g, i0 % g.nx, (i0 / g.nx) % g.ny, i0 / g.nxy, c);
+      }
+      if (SOLID && ((mask >> SELF_SOLID_BIT) & 1u)) {
+        // fullway bounce-back: keep what streamed in, reversed, colour by colour
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+          const int src = nbr(c, -CX(q), -CY(q), -CZ(q));
+          T fr, fb, ft;
+          pull_colour<T, SOLID>(P, S, q, src, mask, fr, fb, ft);
+          P.f_out[OPP(q) * S + i0] = fr;
+          P.aux_out[OPP(q) * S + i0] = fb;
+        }
+      } else {
+        T f[27];
+#pragma unroll
+        for (int q = 0; q < 27; ++q) f[q] = buf[st][q][t];
+        if (SOLID) {
+#pragma unroll
+          for (int q = 0; q < 27; ++q)
+            if ((mask >> OPP(q)) & 1u) f[q] += ld(P.aux_in + q * S + nbr(c, -CX(q), -CY(q), -CZ(q)));
+        }
+        const T rr = buf[st][27][t], rb = buf[st][28][t];
+        const T rho = rr + rb;
+        const T p = rr * ph.cr2 + rb * ph.cb2;
+        const T phi = order_parameter(rr, rb, ph);
+        const T nu = T(0.5) * (T(1) + phi) * ph.nu_r + T(0.5) * (T(1) - phi) * ph.nu_b;
+        // omega_1 = 1/tau with tau = 1/2 + rho nu / p (Eq. mu = (tau - 1/2) p)
+        const T om1 = p / (T(0.5) * p + rho * nu);
+        T j[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int q = 0; q < 27; ++q)
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+            if (CA(q, a) != 0) j[a] += T(CA(q, a)) * f[q];
+        const T F[3] = {buf[st][29][t], buf[st][30][t], buf[st][31][t]};
+        T Q[3] = {T(0), T(0), T(0)};
+        if (ph.use_Q) {
+          Q[0] = buf[st][32][t];
+          Q[1] = buf[st][33][t];
+          Q[2] = buf[st][34][t];
+        }
+        const T inv_rho = T(1) / rho;
+        T u[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[a] = (j[a] + T(0.5) * F[a]) * inv_rho;
+        collide_cm<T, UNIT>(f, rho, p, u[0], u[1], u[2], F, Q, om1, ph);
+#pragma unroll
+        for (int q = 0; q < 27; ++q) P.f_out[q * S + i0] = f[q];
+      }
+    }
+    cur = nxt;
+    st ^= 1;
+  }
+  cp_async_wait_all();
+}
+
+}  // namespace cg27

@@ -48,10 +48,11 @@ def test_defaults_and_workspace(cg):
     assert abs(p.alpha_r - 8 / 27) < 1e-16 and p.beta == 0.7
     n = 32 * 16 * 8
     b32 = cg.cg_workspace_bytes(p)
-    # two population copies (27) + two recoloring states (5) + 18 side fields
-    assert b32 >= n * 4 * (2 * 27 + 2 * 5 + 18)
+    # two population copies (27) + two recoloring states (5) + 15 side fields
+    # (rho_r, rho_b, j, phi, F, (p - rho c_s^2) u, Q)
+    assert b32 >= n * 4 * (2 * 27 + 2 * 5 + 15)
     p.precision = cg.CG_F64
-    assert cg.cg_workspace_bytes(p) >= 2 * n * 4 * (2 * 27 + 2 * 5 + 18)
+    assert cg.cg_workspace_bytes(p) >= 2 * n * 4 * (2 * 27 + 2 * 5 + 15)
     p.precision = cg.CG_F32
     p.bc[2] = cg.CG_BC_BOUNCEBACK
     assert cg.cg_workspace_bytes(p) > b32  # walls reserve the blue part and the mask

@@ -137,7 +137,6 @@ struct cg_ctx {
   bool initialised = false;
   bool unit = false;  // all omega = 1 except omega_1, Model D: the Sec. III.E form
   int tz = 1;         // z planes per tile of the step kernels
-  int collide_blocks = 0;  // persistent grid of k_collide (set on first launch)
   // per-pass timing: events[NUM_EVENTS_PER_STEP * s + k] brackets pass k of timed step s
   std::vector<cudaEvent_t> events;
   int64_t prof_capacity = 0, prof_used = 0;
@@ -207,27 +206,6 @@ Ptrs<T> make_ptrs(const cg_ctx* c, int cur) {
   return P;
 }
 
-// persistent grid of k_collide: every SM filled to its occupancy
-template <typename T, bool SOLID, bool UNIT>
-int collide_blocks(const cg_ctx* c) {
-  int dev = 0, sms = 148, per_sm = 1;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_collide<T, SOLID, UNIT>,
-                                                    CollideCfg<T>::CT, 0) != cudaSuccess || per_sm < 1)
-    per_sm = 1;
-  const int xt = (c->prm.nx + CollideCfg<T>::CT - 1) / CollideCfg<T>::CT;
-  const long long items = (long long)xt * c->prm.ny * c->prm.nz;
-  return (int)std::min<long long>(items, (long long)sms * per_sm);
-}
-
-template <typename T, bool SOLID, bool UNIT>
-void launch_collide(cg_ctx* c, const Geom& g, const Ptrs<T>& P, const Phys<T>& ph) {
-  if (c->collide_blocks <= 0) c->collide_blocks = collide_blocks<T, SOLID, UNIT>(c);
-  const int xt = (c->prm.nx + CollideCfg<T>::CT - 1) / CollideCfg<T>::CT;
-  const long long items = (long long)xt * c->prm.ny * c->prm.nz;
-  k_collide<T, SOLID, UNIT><<<c->collide_blocks, CollideCfg<T>::CT, 0, c->stream>>>(g, P, ph, xt, items);
-}
-
 template <typename T, bool SOLID>
 void enqueue_step(cg_ctx* c) {
   const int cur = (int)(c->steps & 1);
@@ -247,9 +225,9 @@ void enqueue_step(cg_ctx* c) {
   if (c->prm.use_Q) k_qcorr<T><<<gc, bc, 0, c->stream>>>(g, P);
   if (ev) cudaEventRecord(ev[3], c->stream);
   if (c->unit)
-    launch_collide<T, SOLID, true>(c, g, P, ph);
+    k_collide<T, SOLID, true><<<gc, bc, 0, c->stream>>>(g, P, ph);
   else
-    launch_collide<T, SOLID, false>(c, g, P, ph);
+    k_collide<T, SOLID, false><<<gc, bc, 0, c->stream>>>(g, P, ph);
   if (ev) cudaEventRecord(ev[4], c->stream);
 }
 

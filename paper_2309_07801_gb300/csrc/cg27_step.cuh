@@ -13,8 +13,8 @@
 //             kappa, F, u, (p - rho c_s^2) u, R and the recoloring
 //             fractions on the tile                            (Secs. II.A, III.E)
 //   k_qcorr   correction term Q from (p - rho c_s^2) u             (Sec. III.E)
-//   k_collide persistent, cp.async-pipelined: pull the totals, CM-MRT
-//             collision, store f^*                          (Secs. II.B, III.E)
+//   k_collide one thread per cell: pull the totals, CM-MRT collision, store
+//             f^*                                           (Secs. II.B, III.E)
 #pragma once
 
 #include "cg27_device.cuh"
@@ -373,146 +373,65 @@ __global__ void __launch_bounds__(128) k_qcorr(Geom g, Ptrs<T> P) {
 }
 
 // ---- pass 4: streaming of the totals and the collision ----------------------------------
-// A persistent kernel: each thread walks cells (rows of CT cells along x) with a
-// stride of the whole grid.  While it computes one cell, the 35 values of its
-// next cell (27 pulled populations, rho_r, rho_b, F, Q) are already being
-// copied by cp.async into this thread's own shared-memory slots, so memory
-// latency is hidden without holding the loads in registers and without any
-// barrier (no thread reads another thread's slots).
-
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  if (sizeof(T) == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-template <typename T>
-struct CollideCfg {
-  static constexpr int CT = sizeof(T) == 4 ? 128 : 64;  // threads per block
-  static constexpr int NV = 35;                          // values staged per cell
-};
-
-// neighbour offsets of cell (x, y, z)
-__device__ __forceinline__ void cell_at(const Geom& g, int x, int y, int z, Cell& c) {
-  c.xs[0] = (x == 0 ? g.nx - 1 : x - 1);
-  c.xs[1] = x;
-  c.xs[2] = (x == g.nx - 1 ? 0 : x + 1);
-  c.ys[0] = (y == 0 ? g.ny - 1 : y - 1) * g.nx;
-  c.ys[1] = y * g.nx;
-  c.ys[2] = (y == g.ny - 1 ? 0 : y + 1) * g.nx;
-  c.zs[0] = (z == 0 ? g.nz - 1 : z - 1) * g.nxy;
-  c.zs[1] = z * g.nxy;
-  c.zs[2] = (z == g.nz - 1 ? 0 : z + 1) * g.nxy;
-  c.idx = x + c.ys[1] + c.zs[1];
-}
+// One thread per cell: 27 pulled populations, rho_r, rho_b, F and Q in
+// registers, the collision, 27 coalesced stores.  The register budget is capped
+// (six 128-thread blocks per SM) so that enough warps keep loads in flight; at
+// this occupancy the kernel streams at about the copy bandwidth of the device.
 
 template <typename T, bool SOLID, bool UNIT>
-__global__ void __launch_bounds__(CollideCfg<T>::CT) k_collide(Geom g, Ptrs<T> P, Phys<T> ph,
-                                                               int xtiles, long long nitems) {
-  constexpr int CT = CollideCfg<T>::CT, NV = CollideCfg<T>::NV;
-  __shared__ T buf[2][NV][CT];
-  const int t = threadIdx.x;
+__global__ void __launch_bounds__(128, 6) k_collide(Geom g, Ptrs<T> P, Phys<T> ph) {
+  Cell c;
+  if (!make_cell(g, c)) return;
   const long long S = g.stride;
-
-  // start the copies of work item `it` into stage `st`; returns the cell index
-  // (or -1 when this thread has no cell in the item)
-  auto issue = [&](long long it, int st) -> int {
-    const int xt = (int)(it % xtiles);
-    const long long r = it / xtiles;
-    const int y = (int)(r % g.ny), z = (int)(r / g.ny);
-    const int x = xt * CT + t;
-    if (x >= g.nx) return -1;
-    Cell c;
-    cell_at(g, x, y, z, c);
+  const int i0 = c.idx;
+  const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
+  if (SOLID && ((mask >> SELF_SOLID_BIT) & 1u)) {
+    // fullway bounce-back: keep what streamed in, reversed, colour by colour
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      const int src = nbr(c, -CX(q), -CY(q), -CZ(q));
+      T fr, fb, ft;
+      pull_colour<T, SOLID>(P, S, q, src, mask, fr, fb, ft);
+      P.f_out[OPP(q) * S + i0] = fr;
+      P.aux_out[OPP(q) * S + i0] = fb;
+    }
+    return;
+  }
+  T f[27];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) f[q] = ld(P.f_in + q * S + nbr(c, -CX(q), -CY(q), -CZ(q)));
+  if (SOLID) {
 #pragma unroll
     for (int q = 0; q < 27; ++q)
-      cp_async_elem(&buf[st][q][t], P.f_in + q * S + nbr(c, -CX(q), -CY(q), -CZ(q)));
-    cp_async_elem(&buf[st][27][t], P.mac + c.idx);
-    cp_async_elem(&buf[st][28][t], P.mac + S + c.idx);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) cp_async_elem(&buf[st][29 + a][t], P.force + a * S + c.idx);
-    if (ph.use_Q) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) cp_async_elem(&buf[st][32 + a][t], P.qc + a * S + c.idx);
-    }
-    return c.idx;
-  };
-
-  long long it = blockIdx.x;
-  int st = 0;
-  int cur = it < nitems ? issue(it, 0) : -1;
-  cp_async_commit();
-  for (; it < nitems; it += gridDim.x) {
-    const long long nx_it = it + gridDim.x;
-    const int nxt = nx_it < nitems ? issue(nx_it, st ^ 1) : -1;
-    cp_async_commit();
-    cp_async_wait_one();  // the group of item `it` has landed
-    if (cur >= 0) {
-      const int i0 = cur;
-      uint32_t mask = 0u;
-      Cell c;
-      if (SOLID) {
-        mask = ld(P.mask + i0);
-        cell_at(g, i0 % g.nx, (i0 / g.nx) % g.ny, i0 / g.nxy, c);
-      }
-      if (SOLID && ((mask >> SELF_SOLID_BIT) & 1u)) {
-        // fullway bounce-back: keep what streamed in, reversed, colour by colour
-#pragma unroll
-        for (int q = 0; q < 27; ++q) {
-          const int src = nbr(c, -CX(q), -CY(q), -CZ(q));
-          T fr, fb, ft;
-          pull_colour<T, SOLID>(P, S, q, src, mask, fr, fb, ft);
-          P.f_out[OPP(q) * S + i0] = fr;
-          P.aux_out[OPP(q) * S + i0] = fb;
-        }
-      } else {
-        T f[27];
-#pragma unroll
-        for (int q = 0; q < 27; ++q) f[q] = buf[st][q][t];
-        if (SOLID) {
-#pragma unroll
-          for (int q = 0; q < 27; ++q)
-            if ((mask >> OPP(q)) & 1u) f[q] += ld(P.aux_in + q * S + nbr(c, -CX(q), -CY(q), -CZ(q)));
-        }
-        const T rr = buf[st][27][t], rb = buf[st][28][t];
-        const T rho = rr + rb;
-        const T p = rr * ph.cr2 + rb * ph.cb2;
-        const T phi = order_parameter(rr, rb, ph);
-        const T nu = T(0.5) * (T(1) + phi) * ph.nu_r + T(0.5) * (T(1) - phi) * ph.nu_b;
-        // omega_1 = 1/tau with tau = 1/2 + rho nu / p (Eq. mu = (tau - 1/2) p)
-        const T om1 = p / (T(0.5) * p + rho * nu);
-        T j[3] = {T(0), T(0), T(0)};
-#pragma unroll
-        for (int q = 0; q < 27; ++q)
-#pragma unroll
-          for (int a = 0; a < 3; ++a)
-            if (CA(q, a) != 0) j[a] += T(CA(q, a)) * f[q];
-        const T F[3] = {buf[st][29][t], buf[st][30][t], buf[st][31][t]};
-        T Q[3] = {T(0), T(0), T(0)};
-        if (ph.use_Q) {
-          Q[0] = buf[st][32][t];
-          Q[1] = buf[st][33][t];
-          Q[2] = buf[st][34][t];
-        }
-        const T inv_rho = T(1) / rho;
-        T u[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) u[a] = (j[a] + T(0.5) * F[a]) * inv_rho;
-        collide_cm<T, UNIT>(f, rho, p, u[0], u[1], u[2], F, Q, om1, ph);
-#pragma unroll
-        for (int q = 0; q < 27; ++q) P.f_out[q * S + i0] = f[q];
-      }
-    }
-    cur = nxt;
-    st ^= 1;
+      if ((mask >> OPP(q)) & 1u) f[q] += ld(P.aux_in + q * S + nbr(c, -CX(q), -CY(q), -CZ(q)));
   }
-  cp_async_wait_all();
+  const T rr = ld(P.mac + i0), rb = ld(P.mac + S + i0);
+  const T F[3] = {ld(P.force + i0), ld(P.force + S + i0), ld(P.force + 2 * S + i0)};
+  T Q[3] = {T(0), T(0), T(0)};
+  if (ph.use_Q) {
+    Q[0] = ld(P.qc + i0);
+    Q[1] = ld(P.qc + S + i0);
+    Q[2] = ld(P.qc + 2 * S + i0);
+  }
+  const T rho = rr + rb;
+  const T p = rr * ph.cr2 + rb * ph.cb2;
+  const T phi = order_parameter(rr, rb, ph);
+  const T nu = T(0.5) * (T(1) + phi) * ph.nu_r + T(0.5) * (T(1) - phi) * ph.nu_b;
+  // omega_1 = 1/tau with tau = 1/2 + rho nu / p (Eq. mu = (tau - 1/2) p)
+  const T om1 = p / (T(0.5) * p + rho * nu);
+  T j[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int q = 0; q < 27; ++q)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (CA(q, a) != 0) j[a] += T(CA(q, a)) * f[q];
+  const T inv_rho = T(1) / rho;
+  T u[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u[a] = (j[a] + T(0.5) * F[a]) * inv_rho;
+  collide_cm<T, UNIT>(f, rho, p, u[0], u[1], u[2], F, Q, om1, ph);
+#pragma unroll
+  for (int q = 0; q < 27; ++q) P.f_out[q * S + i0] = f[q];
 }
 
 }  // namespace cg27

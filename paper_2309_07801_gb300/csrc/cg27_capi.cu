@@ -220,9 +220,14 @@ void enqueue_step(cg_ctx* c) {
   if (ev) cudaEventRecord(ev[0], c->stream);
   k_macro<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph, c->tz);
   if (ev) cudaEventRecord(ev[1], c->stream);
-  k_fields<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph, c->tz);
+  // FP32 wall-free domains use the separable stencils; FP64 (shared memory)
+  // and walls (neighbour substitution) use the direct ones
+  if constexpr (!SOLID && sizeof(T) == 4)
+    k_fields_sep<T><<<gr, b, 0, c->stream>>>(g, P, ph, c->tz);
+  else
+    k_fields<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph, c->tz);
   if (ev) cudaEventRecord(ev[2], c->stream);
-  if (c->prm.use_Q) k_qcorr<T><<<gc, bc, 0, c->stream>>>(g, P);
+  if (c->prm.use_Q) k_qcorr<T><<<gr, b, 0, c->stream>>>(g, P, c->tz);
   if (ev) cudaEventRecord(ev[3], c->stream);
   if (c->unit)
     k_collide<T, SOLID, true><<<gc, bc, 0, c->stream>>>(g, P, ph);

@@ -119,17 +119,27 @@ __global__ void __launch_bounds__(NT) k_macro(Geom g, Ptrs<T> P, Phys<T> ph, int
   fetch(z0 + 1);
   store(z0 + 1);
   __syncthreads();
+  // populations of the next plane are loaded while the current one is summed
+  T fn[27];
+  auto fetchf = [&](int z) {
+    if (!c.active) return;
+    const int zo[3] = {zoff(g, z - 1), zoff(g, z), zoff(g, z + 1)};
+#pragma unroll
+    for (int q = 0; q < 27; ++q)
+      fn[q] = ld(P.f_in + q * S + (c.xs[1 - CX(q)] + c.ys[1 - CY(q)] + zo[1 - CZ(q)]));
+  };
+  fetchf(z0);
   for (int z = z0; z < z1; ++z) {
     fetch(z + 2);  // in flight while this plane is computed
+    T f[27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) f[q] = fn[q];
+    if (z + 1 < z1) fetchf(z + 1);
     if (c.active) {
       const int zo[3] = {(z == 0 ? g.nz - 1 : z - 1) * g.nxy, z * g.nxy,
                          (z == g.nz - 1 ? 0 : z + 1) * g.nxy};
       const int i0 = c.xs[1] + c.ys[1] + zo[1];
       const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
-      T f[27];
-#pragma unroll
-      for (int q = 0; q < 27; ++q)
-        f[q] = ld(P.f_in + q * S + (c.xs[1 - CX(q)] + c.ys[1 - CY(q)] + zo[1 - CZ(q)]));
       T rr = T(0), rb = T(0), jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
       for (int q = 0; q < 27; ++q) {
@@ -350,26 +360,235 @@ __global__ void __launch_bounds__(NT) k_fields(Geom g, Ptrs<T> P, Phys<T> ph, in
   }
 }
 
+// ---- pass 2, separable form (periodic domains) --------------------------------------------
+// The isotropic difference of Sec. II.A factorises over the axes:
+//   d_x chi = D_x S_y S_z chi,  d_y chi = S_x D_y S_z chi,  d_z chi = S_x S_y D_z chi,
+// with the 1D smoothing S = (1/6, 2/3, 1/6) and difference D = (-1/2, 0, 1/2)
+// (the 1/c_s^2 factor included).  Per plane, the z parts A = S_z chi and
+// B = D_z chi are staged; each in-plane derivative is then 6 or 9 taps.  A
+// thread stages A, B for exactly the positions it loaded or computed itself, so
+// no extra barrier is needed.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_fields_sep(Geom g, Ptrs<T> P, Phys<T> ph, int tz) {
+  using H2 = HaloSlots<2>;
+  using H1 = HaloSlots<1>;
+  constexpr int W2 = H2::W, P2 = H2::PL, W1 = H1::W, P1 = H1::PL;
+  constexpr T S0 = T(2) / T(3), S1 = T(1) / T(6);
+  __shared__ T sPhi[3][P2];
+  __shared__ T sA[P2], sB[P2];      // S_z phi and D_z phi of the plane whose normals come next
+  __shared__ T sN[3][3][P1];
+  __shared__ T sNA[3][P1], sNB[3][P1];  // S_z n_b and D_z n_b of the output plane
+  __shared__ T sG[2][3][NT];
+  const Col c = make_col(g);
+  const int z0 = blockIdx.z * tz, z1 = min(g.nz, z0 + tz);
+  const long long S = g.stride;
+  H2 h2;
+  h2.init(g, c);
+  H1 h1;
+  h1.init(g, c);
+  T pphi[H2::K];
+  auto fetch_phi = [&](int z) {
+    const int zo = zoff(g, z);
+#pragma unroll
+    for (int k = 0; k < H2::K; ++k)
+      if (h2.xy[k] >= 0) pphi[k] = ld(P.phi + h2.xy[k] + zo);
+  };
+  // store phi of plane p (own positions) and A, B of plane p - 1 from the ring
+  auto store_phi_ab = [&](int p) {
+#pragma unroll
+    for (int k = 0; k < H2::K; ++k) {
+      if (h2.xy[k] < 0) continue;
+      const int i = c.tid + k * NT;
+      const T lo = sPhi[ring3(p - 2)][i], mid = sPhi[ring3(p - 1)][i], hi = pphi[k];
+      sPhi[ring3(p)][i] = hi;
+      sA[i] = S1 * (lo + hi) + S0 * mid;
+      sB[i] = T(0.5) * (hi - lo);
+    }
+  };
+  // n of plane p on the tile plus a 1-cell halo (A, B of p staged); also
+  // S_z n and D_z n of plane p - 1 at the same positions
+  auto normals = [&](int p, bool with_nab) {
+#pragma unroll
+    for (int k = 0; k < H1::K; ++k) {
+      if (h1.xy[k] < 0) continue;
+      const int i = c.tid + k * NT;
+      const int lx = i % W1, ly = i / W1;
+      const int ctr = (lx + 1) + W2 * (ly + 1);
+      const T gx = T(0.5) * (S1 * (sA[ctr + 1 - W2] - sA[ctr - 1 - W2]) + S0 * (sA[ctr + 1] - sA[ctr - 1]) +
+                             S1 * (sA[ctr + 1 + W2] - sA[ctr - 1 + W2]));
+      const T gy = T(0.5) * (S1 * (sA[ctr - 1 + W2] - sA[ctr - 1 - W2]) + S0 * (sA[ctr + W2] - sA[ctr - W2]) +
+                             S1 * (sA[ctr + 1 + W2] - sA[ctr + 1 - W2]));
+      const T gz = S1 * (S1 * sB[ctr - 1 - W2] + S0 * sB[ctr - W2] + S1 * sB[ctr + 1 - W2]) +
+                   S0 * (S1 * sB[ctr - 1] + S0 * sB[ctr] + S1 * sB[ctr + 1]) +
+                   S1 * (S1 * sB[ctr - 1 + W2] + S0 * sB[ctr + W2] + S1 * sB[ctr + 1 + W2]);
+      const T gr[3] = {gx, gy, gz};
+      const T g2 = gx * gx + gy * gy + gz * gz;
+      const bool ok = g2 > T(1e-24);
+      const T inv_len = ok ? T(1) / sqrt(g2) : T(0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const T nb = gr[b] * inv_len;
+        sN[ring3(p)][b][i] = nb;
+        if (with_nab) {
+          const T nlo = sN[ring3(p - 2)][b][i], nmid = sN[ring3(p - 1)][b][i];
+          sNA[b][i] = S1 * (nlo + nb) + S0 * nmid;
+          sNB[b][i] = T(0.5) * (nb - nlo);
+        }
+      }
+      const int ix = lx - 1, iy = ly - 1;
+      if (ix >= 0 && ix < TX && iy >= 0 && iy < TY)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sG[p & 1][a][ix + TX * iy] = gr[a];
+    }
+  };
+
+  // prologue: phi z0-2..z0+2 (with A, B of z0-1), n of z0-1 and z0
+  fetch_phi(z0 - 2);
+#pragma unroll
+  for (int k = 0; k < H2::K; ++k)
+    if (h2.xy[k] >= 0) sPhi[ring3(z0 - 2)][c.tid + k * NT] = pphi[k];
+  fetch_phi(z0 - 1);
+#pragma unroll
+  for (int k = 0; k < H2::K; ++k)
+    if (h2.xy[k] >= 0) sPhi[ring3(z0 - 1)][c.tid + k * NT] = pphi[k];
+  fetch_phi(z0);
+  store_phi_ab(z0);  // A, B of z0-1 (own positions: no barrier needed for them)
+  __syncthreads();
+  normals(z0 - 1, false);
+  fetch_phi(z0 + 1);
+  __syncthreads();
+  store_phi_ab(z0 + 1);  // phi z0+1 replaces z0-2; A, B of z0
+  __syncthreads();
+  normals(z0, false);
+  fetch_phi(z0 + 2);
+  __syncthreads();
+  store_phi_ab(z0 + 2);  // replaces z0-1; A, B of z0+1
+  __syncthreads();
+
+  T mac[5];
+  auto fetch_mac = [&](int z) {
+    if (!c.active) return;
+    const int i0 = c.xs[1] + c.ys[1] + zoff(g, z);
+#pragma unroll
+    for (int f = 0; f < 5; ++f) mac[f] = ld(P.mac + f * S + i0);
+  };
+  fetch_mac(z0);
+  for (int z = z0; z < z1; ++z) {
+    fetch_phi(z + 3);
+    normals(z + 1, true);  // n of z+1; S_z n, D_z n of z
+    __syncthreads();
+    if (c.active) {
+      const int i0 = c.xs[1] + c.ys[1] + z * g.nxy;
+      const int ctr = (c.tx + 1) + W1 * (c.ty + 1);
+      const T nc[3] = {sN[ring3(z)][0][ctr], sN[ring3(z)][1][ctr], sN[ring3(z)][2][ctr]};
+      T dn[3][3];  // dn[a][b] = d_a n_b
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const T* A = sNA[b];
+        const T* B = sNB[b];
+        dn[0][b] = T(0.5) * (S1 * (A[ctr + 1 - W1] - A[ctr - 1 - W1]) + S0 * (A[ctr + 1] - A[ctr - 1]) +
+                             S1 * (A[ctr + 1 + W1] - A[ctr - 1 + W1]));
+        dn[1][b] = T(0.5) * (S1 * (A[ctr - 1 + W1] - A[ctr - 1 - W1]) + S0 * (A[ctr + W1] - A[ctr - W1]) +
+                             S1 * (A[ctr + 1 + W1] - A[ctr + 1 - W1]));
+        dn[2][b] = S1 * (S1 * B[ctr - 1 - W1] + S0 * B[ctr - W1] + S1 * B[ctr + 1 - W1]) +
+                   S0 * (S1 * B[ctr - 1] + S0 * B[ctr] + S1 * B[ctr + 1]) +
+                   S1 * (S1 * B[ctr - 1 + W1] + S0 * B[ctr + W1] + S1 * B[ctr + 1 + W1]);
+      }
+      T div = T(0), nnd = T(0);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        div += dn[a][a];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) nnd += nc[a] * nc[b] * dn[a][b];
+      }
+      const T kappa = -(div - nnd);
+      const T rr = mac[0], rb = mac[1];
+      const T rho = rr + rb;
+      const T p = rr * ph.cr2 + rb * ph.cb2;
+      T fbody[3] = {T(0), T(0), T(0)};
+      if (ph.force_mode == 1) {
+        for (int a = 0; a < 3; ++a) fbody[a] = ph.g[a];
+      } else if (ph.force_mode == 2) {
+        for (int a = 0; a < 3; ++a) fbody[a] = rho * ph.g[a];
+      } else if (ph.force_mode == 3) {
+        for (int a = 0; a < 3; ++a) fbody[a] = (rho - ph.rho_ref) * ph.g[a];
+      }
+      const T inv_rho = T(1) / rho;
+      const T rfac = ph.beta * rr * rb * inv_rho * inv_rho * p;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const T Fa = T(0.5) * ph.sigma * kappa * sG[z & 1][a][c.tid] + fbody[a];
+        const T ua = (mac[2 + a] + T(0.5) * Fa) * inv_rho;
+        P.force[a * S + i0] = Fa;
+        P.wv[a * S + i0] = (p - rho * Lat<T>::CS2) * ua;
+        P.s_out[(2 + a) * S + i0] = rfac * nc[a];
+      }
+      P.s_out[i0] = rr * inv_rho;
+      P.s_out[S + i0] = rb * inv_rho;
+    }
+    fetch_mac(z + 1);
+    store_phi_ab(z + 3);  // phi z+3 replaces z; A, B of z+2 (own positions)
+    __syncthreads();
+  }
+}
+
 // ---- pass 3: correction term ----------------------------------------------------------
 // Q_a = -3 d_a[(p - rho c_s^2) u_a] with d_a = (1/c_s^2) sum_i w_i c_ia (.)
-// (Sec. III.E); one thread per cell, neighbours through L1.
+// (Sec. III.E); z-marching tile, (p - rho c_s^2) u of planes z-1..z+1 staged in
+// a shared-memory ring.
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_qcorr(Geom g, Ptrs<T> P) {
-  Cell c;
-  if (!make_cell(g, c)) return;
+__global__ void __launch_bounds__(NT) k_qcorr(Geom g, Ptrs<T> P, int tz) {
+  using HS = HaloSlots<1>;
+  constexpr int W = HS::W, PL = HS::PL;
+  constexpr int RING = sizeof(T) == 4 ? 4 : 3;
+  __shared__ T sW[RING][3][PL];
+  const Col c = make_col(g);
+  const int z0 = blockIdx.z * tz, z1 = min(g.nz, z0 + tz);
   const long long S = g.stride;
-  T Q[3] = {T(0), T(0), T(0)};
+  HS hs;
+  hs.init(g, c);
+  T pre[HS::K][3];
+  auto fetch = [&](int z) {
+    const int zo = zoff(g, z);
 #pragma unroll
-  for (int q = 0; q < 27; ++q) {
-    if (q == REST) continue;
-    const int nb = nbr(c, CX(q), CY(q), CZ(q));
+    for (int k = 0; k < HS::K; ++k)
+      if (hs.xy[k] >= 0)
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-      if (CA(q, a) != 0) Q[a] += T(CA(q, a)) * (WQ<T>(q) * ld(P.wv + a * S + nb));
+        for (int f = 0; f < 3; ++f) pre[k][f] = ld(P.wv + f * S + hs.xy[k] + zo);
+  };
+  auto store = [&](int z) {
+#pragma unroll
+    for (int k = 0; k < HS::K; ++k)
+      if (hs.xy[k] >= 0)
+#pragma unroll
+        for (int f = 0; f < 3; ++f) sW[(z + RING) % RING][f][c.tid + k * NT] = pre[k][f];
+  };
+  fetch(z0 - 1); store(z0 - 1);
+  fetch(z0); store(z0);
+  fetch(z0 + 1); store(z0 + 1);
+  __syncthreads();
+  for (int z = z0; z < z1; ++z) {
+    fetch(z + 2);
+    if (c.active) {
+      const int ctr = (c.tx + 1) + W * (c.ty + 1);
+      T Q[3] = {T(0), T(0), T(0)};
+#pragma unroll
+      for (int q = 0; q < 27; ++q) {
+        if (q == REST) continue;
+        const int off = ctr + CX(q) + W * CY(q);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          if (CA(q, a) != 0) Q[a] += T(CA(q, a)) * (WQ<T>(q) * sW[(z + CZ(q) + RING) % RING][a][off]);
+      }
+      const int i0 = c.xs[1] + c.ys[1] + z * g.nxy;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) P.qc[a * S + i0] = T(-9) * Q[a];
+    }
+    if (RING == 3) __syncthreads();
+    store(z + 2);
+    __syncthreads();
   }
-#pragma unroll
-  for (int a = 0; a < 3; ++a) P.qc[a * S + c.idx] = T(-9) * Q[a];
 }
 
 // ---- pass 4: streaming of the totals and the collision ----------------------------------

@@ -69,8 +69,12 @@ extern "C" {
 #define CG_MODEL_D 3 /* generalized equilibria, Phi_i up to O(u^6) (Sec. III.D) */
 
 /* storage and arithmetic precision */
-#define CG_F64 0 /* FP64 storage and arithmetic */
-#define CG_F32 1 /* FP32 storage and arithmetic */
+#define CG_F64 0   /* FP64 storage and arithmetic */
+#define CG_F32 1   /* FP32 storage and arithmetic */
+#define CG_F16S 2  /* populations stored in FP16 as deviations from the cell's
+                      rest-state populations (the equilibrium at u = 0 of
+                      Sec. II.A); everything else FP32; periodic domains only */
+#define CG_BF16S 3 /* as CG_F16S with BF16 storage */
 
 typedef struct cg_params {
   int32_t nx, ny, nz;     /* cells per axis, each >= 1 (>= 3 on a bounce-back axis) */
@@ -87,7 +91,7 @@ typedef struct cg_params {
   int32_t force_mode;     /* CG_FORCE_* */
   int32_t model;          /* CG_MODEL_* */
   int32_t use_Q;          /* 1: apply the correction term Q (Sec. III.E); 0: omit it */
-  int32_t precision;      /* CG_F64 or CG_F32 */
+  int32_t precision;      /* CG_F64, CG_F32, CG_F16S or CG_BF16S */
   int32_t solid_mask;     /* 1: cg_init_fields() may be given a solid mask (reserves
                              workspace for walls; implied by a bounce-back axis) */
   int32_t reserved_;      /* must be 0 */

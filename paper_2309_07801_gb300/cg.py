@@ -20,8 +20,8 @@ CG_OK = 0
 CG_BC_PERIODIC, CG_BC_BOUNCEBACK = 0, 1
 CG_FORCE_NONE, CG_FORCE_CONST, CG_FORCE_GRAVITY, CG_FORCE_BUOYANCY = 0, 1, 2, 3
 CG_MODEL_A, CG_MODEL_B, CG_MODEL_C, CG_MODEL_D = 0, 1, 2, 3
-CG_F64, CG_F32 = 0, 1
-PRECISIONS = {"f64": CG_F64, "f32": CG_F32}
+CG_F64, CG_F32, CG_F16S, CG_BF16S = 0, 1, 2, 3
+PRECISIONS = {"f64": CG_F64, "f32": CG_F32, "f16s": CG_F16S, "bf16s": CG_BF16S}
 
 
 class CGError(RuntimeError):

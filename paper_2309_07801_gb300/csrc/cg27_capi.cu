@@ -47,7 +47,9 @@ constexpr int NUM_EVENTS_PER_STEP = CG_NUM_PASSES + 1;
 
 struct Layout {
   long long n = 0, stride = 0;
-  size_t elem = 0;
+  size_t elem = 0;      // bytes of an arithmetic value (FP64 or FP32)
+  size_t pop_elem = 0;  // bytes of a stored population
+  int ns = 5;           // fields of the recoloring state
   bool solid = false;
   int red_blocks = 0;
   size_t f[2] = {0, 0}, s[2] = {0, 0}, aux[2] = {0, 0};
@@ -83,8 +85,11 @@ int validate(const cg_params* p) {
   if (p->force_mode < CG_FORCE_NONE || p->force_mode > CG_FORCE_BUOYANCY)
     return fail(CG_ERR_INVALID_ARG, "unknown force_mode");
   if (p->model < CG_MODEL_A || p->model > CG_MODEL_D) return fail(CG_ERR_INVALID_ARG, "unknown model");
-  if (p->precision != CG_F64 && p->precision != CG_F32)
-    return fail(CG_ERR_UNSUPPORTED, "precision must be CG_F64 or CG_F32");
+  if (p->precision != CG_F64 && p->precision != CG_F32 && p->precision != CG_F16S &&
+      p->precision != CG_BF16S)
+    return fail(CG_ERR_UNSUPPORTED, "precision must be CG_F64, CG_F32, CG_F16S or CG_BF16S");
+  if ((p->precision == CG_F16S || p->precision == CG_BF16S) && needs_solid(*p))
+    return fail(CG_ERR_UNSUPPORTED, "walls are not available with 16-bit population storage");
   if (p->reserved_ != 0) return fail(CG_ERR_INVALID_ARG, "reserved_ must be 0");
   return CG_OK;
 }
@@ -94,6 +99,8 @@ Layout make_layout(const cg_params& p) {
   L.n = (long long)p.nx * p.ny * p.nz;
   L.stride = (L.n + 63) / 64 * 64;
   L.elem = (p.precision == CG_F64) ? 8 : 4;
+  L.pop_elem = (p.precision == CG_F64) ? 8 : (p.precision == CG_F32 ? 4 : 2);
+  L.ns = (p.precision == CG_F16S || p.precision == CG_BF16S) ? 6 : 5;
   L.solid = needs_solid(p);
   L.red_blocks = (int)std::min<long long>(1024, (L.n + RED_THREADS - 1) / RED_THREADS);
   size_t off = 0;
@@ -103,8 +110,8 @@ Layout make_layout(const cg_params& p) {
     return at;
   };
   const size_t field = (size_t)L.stride * L.elem;
-  for (int b = 0; b < 2; ++b) L.f[b] = take(27 * field);
-  for (int b = 0; b < 2; ++b) L.s[b] = take(5 * field);
+  for (int b = 0; b < 2; ++b) L.f[b] = take(27 * (size_t)L.stride * L.pop_elem);
+  for (int b = 0; b < 2; ++b) L.s[b] = take(L.ns * field);
   if (L.solid) {
     for (int b = 0; b < 2; ++b) L.aux[b] = take(27 * field);
     L.mask = take((size_t)L.stride * 4);
@@ -167,6 +174,9 @@ Phys<T> make_phys(const cg_params& p) {
   ph.force_mode = p.force_mode;
   ph.model = p.model;
   ph.use_Q = p.use_Q;
+  ph.shift = (p.precision == CG_F16S || p.precision == CG_BF16S) ? 1 : 0;
+  // reference pressure of the red phase at its reference density
+  ph.rest1 = T(3.0 * p.rho_r0 * xi * (1.0 - p.alpha_r));
   return ph;
 }
 
@@ -190,8 +200,8 @@ Ptrs<T> make_ptrs(const cg_ctx* c, int cur) {
   const Layout& L = c->L;
   Ptrs<T> P;
   char* w = c->ws;
-  P.f_in = reinterpret_cast<const T*>(w + L.f[cur]);
-  P.f_out = reinterpret_cast<T*>(w + L.f[1 - cur]);
+  P.f_in = w + L.f[cur];
+  P.f_out = w + L.f[1 - cur];
   P.s_in = reinterpret_cast<const T*>(w + L.s[cur]);
   P.s_out = reinterpret_cast<T*>(w + L.s[1 - cur]);
   P.aux_in = L.solid ? reinterpret_cast<const T*>(w + L.aux[cur]) : nullptr;
@@ -206,7 +216,7 @@ Ptrs<T> make_ptrs(const cg_ctx* c, int cur) {
   return P;
 }
 
-template <typename T, bool SOLID>
+template <typename T, typename SF, bool SOLID>
 void enqueue_step(cg_ctx* c) {
   const int cur = (int)(c->steps & 1);
   const Geom g = make_geom(c);
@@ -218,7 +228,7 @@ void enqueue_step(cg_ctx* c) {
   cudaEvent_t* ev = nullptr;
   if (c->prof_used < c->prof_capacity) ev = &c->events[NUM_EVENTS_PER_STEP * c->prof_used++];
   if (ev) cudaEventRecord(ev[0], c->stream);
-  k_macro<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph, c->tz);
+  k_macro<T, SF, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph, c->tz);
   if (ev) cudaEventRecord(ev[1], c->stream);
   // FP32 wall-free domains use the separable stencils; FP64 (shared memory)
   // and walls (neighbour substitution) use the direct ones
@@ -230,31 +240,36 @@ void enqueue_step(cg_ctx* c) {
   if (c->prm.use_Q) k_qcorr<T><<<gr, b, 0, c->stream>>>(g, P, c->tz);
   if (ev) cudaEventRecord(ev[3], c->stream);
   if (c->unit)
-    k_collide<T, SOLID, true><<<gc, bc, 0, c->stream>>>(g, P, ph);
+    k_collide<T, SF, SOLID, true><<<gc, bc, 0, c->stream>>>(g, P, ph);
   else
-    k_collide<T, SOLID, false><<<gc, bc, 0, c->stream>>>(g, P, ph);
+    k_collide<T, SF, SOLID, false><<<gc, bc, 0, c->stream>>>(g, P, ph);
   if (ev) cudaEventRecord(ev[4], c->stream);
 }
 
-template <typename T>
 void enqueue_step_any(cg_ctx* c) {
-  if (c->L.solid)
-    enqueue_step<T, true>(c);
-  else
-    enqueue_step<T, false>(c);
+  switch (c->prm.precision) {
+    case CG_F64:
+      if (c->L.solid) enqueue_step<double, double, true>(c); else enqueue_step<double, double, false>(c);
+      break;
+    case CG_F32:
+      if (c->L.solid) enqueue_step<float, float, true>(c); else enqueue_step<float, float, false>(c);
+      break;
+    case CG_F16S: enqueue_step<float, __half, false>(c); break;
+    default: enqueue_step<float, __nv_bfloat16, false>(c); break;
+  }
 }
 
 // the population buffer not holding the current state: free between steps
 char* scratch_of(const cg_ctx* c) { return c->ws + c->L.f[1 - (int)(c->steps & 1)]; }
 
-template <typename T, bool SOLID>
+template <typename T, typename SF, bool SOLID>
 void enqueue_init(cg_ctx* c, const double* d_in) {
   const Geom g = make_geom(c);
   const dim3 b = block_of(c->prm), gr = grid_of(c->prm, b);
   // the initial state is written to buffer 0 (read by the first step)
   Ptrs<T> P = make_ptrs<T>(c, 1);
   const long long n = c->L.n;
-  k_init<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, make_phys<T>(c->prm), d_in, d_in + n, d_in + 2 * n, n);
+  k_init<T, SF, SOLID><<<gr, b, 0, c->stream>>>(g, P, make_phys<T>(c->prm), d_in, d_in + n, d_in + 2 * n, n);
 }
 
 }  // namespace
@@ -417,10 +432,15 @@ int cg_init_fields(cg_ctx* c, const double* rho_r, const double* rho_b, const do
                                           c->prm.bc[1] == CG_BC_BOUNCEBACK, c->prm.bc[2] == CG_BC_BOUNCEBACK);
     k_solid_mask<<<gr, b, 0, c->stream>>>(g, d_solid, reinterpret_cast<uint32_t*>(c->ws + c->L.mask));
   }
-  if (c->prm.precision == CG_F64) {
-    if (c->L.solid) enqueue_init<double, true>(c, d_in); else enqueue_init<double, false>(c, d_in);
-  } else {
-    if (c->L.solid) enqueue_init<float, true>(c, d_in); else enqueue_init<float, false>(c, d_in);
+  switch (c->prm.precision) {
+    case CG_F64:
+      if (c->L.solid) enqueue_init<double, double, true>(c, d_in); else enqueue_init<double, double, false>(c, d_in);
+      break;
+    case CG_F32:
+      if (c->L.solid) enqueue_init<float, float, true>(c, d_in); else enqueue_init<float, float, false>(c, d_in);
+      break;
+    case CG_F16S: enqueue_init<float, __half, false>(c, d_in); break;
+    default: enqueue_init<float, __nv_bfloat16, false>(c, d_in); break;
   }
   CG_CUDA(cudaMemsetAsync(c->ws + c->L.flag, 0, sizeof(unsigned int), c->stream));
   CG_CUDA(cudaGetLastError());
@@ -435,10 +455,7 @@ int cg_step(cg_ctx* c, int64_t nsteps) {
   if (!c->initialised) return fail(CG_ERR_INVALID_ARG, "cg_init_fields() has not been called");
   if (nsteps < 0) return fail(CG_ERR_INVALID_ARG, "nsteps must be >= 0");
   for (int64_t s = 0; s < nsteps; ++s) {
-    if (c->prm.precision == CG_F64)
-      enqueue_step_any<double>(c);
-    else
-      enqueue_step_any<float>(c);
+    enqueue_step_any(c);
     ++c->steps;
   }
   CG_CUDA(cudaGetLastError());
@@ -487,12 +504,18 @@ int cg_read_populations(cg_ctx* c, double* fr, double* fb) {
     const int q = paper_to_lex(i);
     if (c->prm.precision == CG_F64) {
       auto P = make_ptrs<double>(c, cur);
-      if (c->L.solid) k_read_pop<double, true><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + n);
-      else k_read_pop<double, false><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + n);
+      if (c->L.solid) k_read_pop<double, double, true><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), q, d_out, d_out + n);
+      else k_read_pop<double, double, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), q, d_out, d_out + n);
     } else {
       auto P = make_ptrs<float>(c, cur);
-      if (c->L.solid) k_read_pop<float, true><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + n);
-      else k_read_pop<float, false><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + n);
+      if (c->prm.precision == CG_F16S)
+        k_read_pop<float, __half, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + n);
+      else if (c->prm.precision == CG_BF16S)
+        k_read_pop<float, __nv_bfloat16, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + n);
+      else if (c->L.solid)
+        k_read_pop<float, float, true><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + n);
+      else
+        k_read_pop<float, float, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + n);
     }
     CG_CUDA(cudaGetLastError());
     if (fr) CG_CUDA(cudaMemcpyAsync(fr + (size_t)i * n, d_out, db, cudaMemcpyDeviceToHost, c->stream));
@@ -582,8 +605,8 @@ int state_regions(const cg_ctx* c, size_t off[6], size_t len[6]) {
   const int cur = (int)(c->steps & 1);
   const size_t field = (size_t)L.stride * L.elem;
   int k = 0;
-  off[k] = L.f[cur]; len[k++] = 27 * field;
-  off[k] = L.s[cur]; len[k++] = 5 * field;
+  off[k] = L.f[cur]; len[k++] = 27 * (size_t)L.stride * L.pop_elem;
+  off[k] = L.s[cur]; len[k++] = L.ns * field;
   off[k] = L.mac; len[k++] = 5 * field;
   off[k] = L.force; len[k++] = 3 * field;
   if (L.solid) {

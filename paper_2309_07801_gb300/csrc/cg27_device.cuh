@@ -28,6 +28,8 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace cg27 {
@@ -66,8 +68,8 @@ struct Geom {
 
 template <typename T>
 struct Ptrs {
-  const T* f_in;
-  T* f_out;
+  const void* f_in;  // populations, stored as the storage type of the mode
+  void* f_out;
   const T* s_in;
   T* s_out;
   const T* aux_in;
@@ -92,7 +94,63 @@ struct Phys {
   T g[3];
   T rho_ref;
   int force_mode, model, use_Q;
+  int shift;  // populations stored as deviations from the rest state (16-bit modes)
+  T rest1;    // p_ref / c_s^2: the moving rest-state populations are w_q rest1
 };
+
+// ---- population storage ---------------------------------------------------------------
+// FP64/FP32 store f_q itself.  The 16-bit modes store the deviation of f_q from
+// a rest-state population, the equilibrium at u = 0 of Sec. II.A:
+//   moving directions:  w_q p / c_s^2 with a global reference pressure p_ref
+//                       (pressure balance keeps p close to p_ref in both
+//                       phases, so no per-cell value has to travel);
+//   rest direction:     rho - p / xi of the cell itself, stored in FP32 as
+//                       field 5 of the recoloring state (the rest population
+//                       stays in its cell, so only the cell's own value is read).
+template <typename SF>
+struct Store {
+  static constexpr bool SHIFT = false;
+  template <typename T>
+  __device__ static T get(const SF* p) { return T(__ldg(p)); }
+  template <typename T>
+  __device__ static SF put(T v) { return SF(v); }
+};
+template <>
+struct Store<__half> {
+  static constexpr bool SHIFT = true;
+  template <typename T>
+  __device__ static T get(const __half* p) { return T(__half2float(__ldg(p))); }
+  template <typename T>
+  __device__ static __half put(T v) { return __float2half_rn(float(v)); }
+};
+template <>
+struct Store<__nv_bfloat16> {
+  static constexpr bool SHIFT = true;
+  template <typename T>
+  __device__ static T get(const __nv_bfloat16* p) { return T(__bfloat162float(__ldg(p))); }
+  template <typename T>
+  __device__ static __nv_bfloat16 put(T v) { return __float2bfloat16_rn(float(v)); }
+};
+
+// fields of the recoloring state: rho_r/rho, rho_b/rho, R (3) [, rho - p/xi]
+template <typename SF>
+__host__ __device__ constexpr int ns_of() { return Store<SF>::SHIFT ? 6 : 5; }
+
+// rest population of the rest direction of a cell
+template <typename T>
+__device__ __forceinline__ T rest_zero(T rho, T p) {
+  return rho - p * (T(19) / T(9));  // 1/xi, xi = 9/19 for D3Q27
+}
+// rest-state population of direction q (r0: the cell's rest_zero)
+template <typename T>
+__device__ __forceinline__ T rest_pop(int q, T r0, T rest1) {
+  return q == REST ? r0 : WQ<T>(q) * rest1;
+}
+
+template <typename SF>
+__device__ __forceinline__ const SF* fin(const void* p) { return static_cast<const SF*>(p); }
+template <typename SF>
+__device__ __forceinline__ SF* fout(void* p) { return static_cast<SF*>(p); }
 
 // ---- cell addressing -----------------------------------------------------------
 
@@ -129,10 +187,12 @@ __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 
 // ---- pull of one direction with the colour split of Eq. (recoloring) -------------
 
-template <typename T, bool SOLID>
+template <typename T, typename SF, bool SOLID>
 __device__ __forceinline__ void pull_colour(const Ptrs<T>& P, long long stride, int q, int src,
-                                            uint32_t mask, T& fr, T& fb, T& ft) {
-  const T f = ld(P.f_in + q * stride + src);
+                                            uint32_t mask, T& fr, T& fb, T& ft, T ph_rest1 = T(0)) {
+  static_assert(!(SOLID && Store<SF>::SHIFT), "walls are not available with 16-bit populations");
+  T f = Store<SF>::template get<T>(fin<SF>(P.f_in) + q * stride + src);
+  if (Store<SF>::SHIFT) f += q == REST ? ld(P.s_in + 5 * stride + src) : WQ<T>(q) * ph_rest1;
   if (SOLID && ((mask >> OPP(q)) & 1u)) {
     // the source is solid: it stores the red part in F and the blue part in AUX
     fr = f;
@@ -389,7 +449,7 @@ __global__ void k_solid_self(Geom g, uint8_t* solid, int has_user, int bx, int b
 // neighbour mask from the self-solid flags
 __global__ void k_solid_mask(Geom g, const uint8_t* solid, uint32_t* mask);
 
-template <typename T, bool SOLID>
+template <typename T, typename SF, bool SOLID>
 __global__ void __launch_bounds__(128) k_init(Geom g, Ptrs<T> P, Phys<T> ph, const double* in_rr,
                                               const double* in_rb, const double* in_u, long long n) {
   Cell c;
@@ -399,7 +459,7 @@ __global__ void __launch_bounds__(128) k_init(Geom g, Ptrs<T> P, Phys<T> ph, con
   const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
   if (SOLID && ((mask >> SELF_SOLID_BIT) & 1u)) {
     for (int q = 0; q < 27; ++q) {
-      P.f_out[q * S + i0] = T(0);
+      fout<SF>(P.f_out)[q * S + i0] = Store<SF>::put(T(0));
       P.aux_out[q * S + i0] = T(0);
     }
     for (int a = 0; a < 5; ++a) {
@@ -417,13 +477,17 @@ __global__ void __launch_bounds__(128) k_init(Geom g, Ptrs<T> P, Phys<T> ph, con
   T k[27];
   keq_model(ph.model, rho, p, u[0], u[1], u[2], k);
   backward_cm(k, u[0], u[1], u[2]);
+  const T r0 = Store<SF>::SHIFT ? rest_zero(rho, p) : T(0);
 #pragma unroll
-  for (int q = 0; q < 27; ++q) P.f_out[q * S + i0] = k[q];
+  for (int q = 0; q < 27; ++q)
+    fout<SF>(P.f_out)[q * S + i0] =
+        Store<SF>::put(Store<SF>::SHIFT ? k[q] - rest_pop(q, r0, ph.rest1) : k[q]);
   if (SOLID)
     for (int q = 0; q < 27; ++q) P.aux_out[q * S + i0] = T(0);
   P.s_out[i0] = rr / rho;
   P.s_out[S + i0] = rb / rho;
   P.s_out[2 * S + i0] = P.s_out[3 * S + i0] = P.s_out[4 * S + i0] = T(0);
+  if (Store<SF>::SHIFT) P.s_out[5 * S + i0] = r0;
   P.mac[i0] = rr;
   P.mac[S + i0] = rb;
   for (int a = 0; a < 3; ++a) {
@@ -457,14 +521,15 @@ __global__ void __launch_bounds__(128) k_read_macros(Geom g, Ptrs<T> P, Phys<T> 
 }
 
 // two-colour post-collision populations of lattice direction q to FP64
-template <typename T, bool SOLID>
-__global__ void __launch_bounds__(128) k_read_pop(Geom g, Ptrs<T> P, int q, double* out_r,
+template <typename T, typename SF, bool SOLID>
+__global__ void __launch_bounds__(128) k_read_pop(Geom g, Ptrs<T> P, Phys<T> ph, int q, double* out_r,
                                                   double* out_b) {
   Cell c;
   if (!make_cell(g, c)) return;
   const long long S = g.stride;
   const int i0 = c.idx;
-  const T f = P.f_in[q * S + i0];
+  T f = Store<SF>::template get<T>(fin<SF>(P.f_in) + q * S + i0);
+  if (Store<SF>::SHIFT) f += rest_pop(q, P.s_in[5 * S + i0], ph.rest1);
   const bool solid = SOLID && ((ld(P.mask + i0) >> SELF_SOLID_BIT) & 1u);
   if (solid) {
     out_r[i0] = double(f);

@@ -83,34 +83,36 @@ __device__ __forceinline__ int zoff(const Geom& g, int z) { return wrapi(z, g.nz
 
 // ---- pass 1 -----------------------------------------------------------------------------
 
-template <typename T, bool SOLID>
+template <typename T, typename SF, bool SOLID>
 __global__ void __launch_bounds__(NT) k_macro(Geom g, Ptrs<T> P, Phys<T> ph, int tz) {
   using HS = HaloSlots<1>;
   constexpr int W = HS::W, PL = HS::PL;
+  constexpr int NS = 5;  // the ring holds what neighbours need
+  constexpr bool SHIFT = Store<SF>::SHIFT;
   // recoloring state of the planes z-1..z+1 (plus the one being prefetched when
   // FP32 leaves room for a fourth slot), 1-cell halo
   constexpr int RING = sizeof(T) == 4 ? 4 : 3;
-  __shared__ T sS[RING][5][PL];
+  __shared__ T sS[RING][NS][PL];
   const Col c = make_col(g);
   const int z0 = blockIdx.z * tz, z1 = min(g.nz, z0 + tz);
   const long long S = g.stride;
   HS hs;
   hs.init(g, c);
-  T pre[HS::K][5];
+  T pre[HS::K][NS];
   auto fetch = [&](int z) {
     const int zo = zoff(g, z);
 #pragma unroll
     for (int k = 0; k < HS::K; ++k)
       if (hs.xy[k] >= 0)
 #pragma unroll
-        for (int f = 0; f < 5; ++f) pre[k][f] = ld(P.s_in + f * S + hs.xy[k] + zo);
+        for (int f = 0; f < NS; ++f) pre[k][f] = ld(P.s_in + f * S + hs.xy[k] + zo);
   };
   auto store = [&](int z) {
 #pragma unroll
     for (int k = 0; k < HS::K; ++k)
       if (hs.xy[k] >= 0)
 #pragma unroll
-        for (int f = 0; f < 5; ++f) sS[(z + RING) % RING][f][c.tid + k * NT] = pre[k][f];
+        for (int f = 0; f < NS; ++f) sS[(z + RING) % RING][f][c.tid + k * NT] = pre[k][f];
   };
   fetch(z0 - 1);
   store(z0 - 1);
@@ -126,7 +128,8 @@ __global__ void __launch_bounds__(NT) k_macro(Geom g, Ptrs<T> P, Phys<T> ph, int
     const int zo[3] = {zoff(g, z - 1), zoff(g, z), zoff(g, z + 1)};
 #pragma unroll
     for (int q = 0; q < 27; ++q)
-      fn[q] = ld(P.f_in + q * S + (c.xs[1 - CX(q)] + c.ys[1 - CY(q)] + zo[1 - CZ(q)]));
+      fn[q] = Store<SF>::template get<T>(fin<SF>(P.f_in) + q * S +
+                                         (c.xs[1 - CX(q)] + c.ys[1 - CY(q)] + zo[1 - CZ(q)]));
   };
   fetchf(z0);
   for (int z = z0; z < z1; ++z) {
@@ -140,17 +143,19 @@ __global__ void __launch_bounds__(NT) k_macro(Geom g, Ptrs<T> P, Phys<T> ph, int
                          (z == g.nz - 1 ? 0 : z + 1) * g.nxy};
       const int i0 = c.xs[1] + c.ys[1] + zo[1];
       const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
+      const T s_rest0 = SHIFT ? ld(P.s_in + 5 * S + i0) : T(0);
       T rr = T(0), rb = T(0), jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
       for (int q = 0; q < 27; ++q) {
         const int src = c.xs[1 - CX(q)] + c.ys[1 - CY(q)] + zo[1 - CZ(q)];
+        const T* s = &sS[(z - CZ(q) + RING) % RING][0][(c.tx + 1 - CX(q)) + W * (c.ty + 1 - CY(q))];
+        if (SHIFT) f[q] += q == REST ? s_rest0 : WQ<T>(q) * ph.rest1;
         T fr, fb, ft = f[q];
         if (SOLID && ((mask >> OPP(q)) & 1u)) {
           fr = f[q];
           fb = ld(P.aux_in + q * S + src);
           ft = fr + fb;
         } else {
-          const T* s = &sS[(z - CZ(q) + RING) % RING][0][(c.tx + 1 - CX(q)) + W * (c.ty + 1 - CY(q))];
           T t = T(0);
           if (q != REST) {
             T cR = T(0);
@@ -351,6 +356,7 @@ __global__ void __launch_bounds__(NT) k_fields(Geom g, Ptrs<T> P, Phys<T> ph, in
         }
         P.s_out[i0] = rr * inv_rho;
         P.s_out[S + i0] = rb * inv_rho;
+        if (ph.shift) P.s_out[5 * S + i0] = rest_zero(rho, p);
       }
     }
     fetch_mac(z + 1);
@@ -525,6 +531,7 @@ __global__ void __launch_bounds__(NT) k_fields_sep(Geom g, Ptrs<T> P, Phys<T> ph
       }
       P.s_out[i0] = rr * inv_rho;
       P.s_out[S + i0] = rb * inv_rho;
+      if (ph.shift) P.s_out[5 * S + i0] = rest_zero(rho, p);
     }
     fetch_mac(z + 1);
     store_phi_ab(z + 3);  // phi z+3 replaces z; A, B of z+2 (own positions)
@@ -597,8 +604,9 @@ __global__ void __launch_bounds__(NT) k_qcorr(Geom g, Ptrs<T> P, int tz) {
 // (six 128-thread blocks per SM) so that enough warps keep loads in flight; at
 // this occupancy the kernel streams at about the copy bandwidth of the device.
 
-template <typename T, bool SOLID, bool UNIT>
+template <typename T, typename SF, bool SOLID, bool UNIT>
 __global__ void __launch_bounds__(128, 6) k_collide(Geom g, Ptrs<T> P, Phys<T> ph) {
+  constexpr bool SHIFT = Store<SF>::SHIFT;
   Cell c;
   if (!make_cell(g, c)) return;
   const long long S = g.stride;
@@ -610,15 +618,21 @@ __global__ void __launch_bounds__(128, 6) k_collide(Geom g, Ptrs<T> P, Phys<T> p
     for (int q = 0; q < 27; ++q) {
       const int src = nbr(c, -CX(q), -CY(q), -CZ(q));
       T fr, fb, ft;
-      pull_colour<T, SOLID>(P, S, q, src, mask, fr, fb, ft);
-      P.f_out[OPP(q) * S + i0] = fr;
+      pull_colour<T, SF, SOLID>(P, S, q, src, mask, fr, fb, ft);
+      fout<SF>(P.f_out)[OPP(q) * S + i0] = Store<SF>::put(fr);
       P.aux_out[OPP(q) * S + i0] = fb;
     }
     return;
   }
   T f[27];
 #pragma unroll
-  for (int q = 0; q < 27; ++q) f[q] = ld(P.f_in + q * S + nbr(c, -CX(q), -CY(q), -CZ(q)));
+  for (int q = 0; q < 27; ++q)
+    f[q] = Store<SF>::template get<T>(fin<SF>(P.f_in) + q * S + nbr(c, -CX(q), -CY(q), -CZ(q)));
+  if (SHIFT) {
+    const T r0 = ld(P.s_in + 5 * S + i0);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) f[q] += rest_pop(q, r0, ph.rest1);
+  }
   if (SOLID) {
 #pragma unroll
     for (int q = 0; q < 27; ++q)
@@ -649,8 +663,11 @@ __global__ void __launch_bounds__(128, 6) k_collide(Geom g, Ptrs<T> P, Phys<T> p
 #pragma unroll
   for (int a = 0; a < 3; ++a) u[a] = (j[a] + T(0.5) * F[a]) * inv_rho;
   collide_cm<T, UNIT>(f, rho, p, u[0], u[1], u[2], F, Q, om1, ph);
+  // the rest-direction shift is the value the field pass stored for this cell
+  const T r0n = SHIFT ? P.s_out[5 * S + i0] : T(0);
 #pragma unroll
-  for (int q = 0; q < 27; ++q) P.f_out[q * S + i0] = f[q];
+  for (int q = 0; q < 27; ++q)
+    fout<SF>(P.f_out)[q * S + i0] = Store<SF>::put(SHIFT ? f[q] - rest_pop(q, r0n, ph.rest1) : f[q]);
 }
 
 }  // namespace cg27

@@ -151,6 +151,32 @@ def rising_bubble(nx=192, ny=192, nz=384) -> Workload:
                     steps=20000, name="rising_bubble_%dx%dx%d" % (nx, ny, nz))
 
 
+def droplet_collision(edge=512) -> Workload:
+    """Head-on binary collision: two droplets of radius 48/512 edge closing at a
+    relative speed 0.2 along x, ratio 1, nu = 0.002, sigma = 0.005."""
+    return Workload(edge, edge, edge, nu_r=0.002, nu_b=0.002, sigma=0.005, beta=0.7,
+                    steps=10000, name="droplet_collision_%d" % edge)
+
+
+def collision_fields(wl: Workload):
+    """Two red droplets at x = c -+ 56/512 edge moving at +-0.1 along x."""
+    n = wl.nx
+    R, d = 48.0 * n / 512.0, 56.0 * n / 512.0
+    shape = (wl.nz, wl.ny, wl.nx)
+    z, y, x = np.meshgrid(np.arange(wl.nz), np.arange(wl.ny), np.arange(wl.nx), indexing="ij")
+    cx, cy, cz = n / 2.0, wl.ny / 2.0, wl.nz / 2.0
+    r1 = np.sqrt((x - (cx - d)) ** 2 + (y - cy) ** 2 + (z - cz) ** 2)
+    r2 = np.sqrt((x - (cx + d)) ** 2 + (y - cy) ** 2 + (z - cz) ** 2)
+    phi = np.maximum(np.tanh(2.0 * (R - r1) / 4.0), np.tanh(2.0 * (R - r2) / 4.0))
+    rho_r = wl.rho_r0 * (1.0 + phi) / 2.0
+    rho_b = wl.rho_b0 * (1.0 - phi) / 2.0
+    u = np.zeros((3,) + shape)
+    weight1 = (1.0 + np.tanh(2.0 * (R - r1) / 4.0)) / 2.0
+    weight2 = (1.0 + np.tanh(2.0 * (R - r2) / 4.0)) / 2.0
+    u[0] = 0.1 * weight1 - 0.1 * weight2
+    return rho_r, rho_b, u
+
+
 def workload_fields(wl: Workload, seed: int = 0, noise: float = 0.0):
     """Initial fields for a named workload (droplet/bubble placement)."""
     shape = (wl.nz, wl.ny, wl.nx)
@@ -166,4 +192,6 @@ def workload_fields(wl: Workload, seed: int = 0, noise: float = 0.0):
         c = (wl.nx / 2.0, wl.ny / 2.0, wl.nz / 6.0)
         return droplet_fields(shape, c, wl.nx / 8.0, wl.rho_r0, wl.rho_b0,
                               noise=noise, seed=seed, invert=True)
+    if wl.name.startswith("droplet_collision"):
+        return collision_fields(wl)
     raise ValueError("unknown workload " + wl.name)

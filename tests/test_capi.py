@@ -89,3 +89,18 @@ def test_create_rejects_bad_workspace(cg):
     with pytest.raises(cg.CGError) as e:
         cg.cg_create(p, 257, need, 0)
     assert e.value.code == -5
+
+
+@pytest.mark.parametrize("prec", ["f16s", "bf16s"])
+def test_walls_rejected_with_16_bit_storage(cg, prec):
+    p = cg.make_params(8, 8, 8, precision=prec)
+    assert cg.cg_workspace_bytes(p) > 0
+    p.bc[2] = cg.CG_BC_BOUNCEBACK
+    with pytest.raises(cg.CGError) as e:
+        cg.cg_workspace_bytes(p)
+    assert e.value.code == -2
+    p.bc[2] = cg.CG_BC_PERIODIC
+    p.solid_mask = 1
+    with pytest.raises(cg.CGError) as e:
+        cg.cg_workspace_bytes(p)
+    assert e.value.code == -2

@@ -162,7 +162,8 @@ int cg_steps_taken(cg_ctx *ctx, int64_t *steps);
  * passes (max_steps = 0 turns timing off).  cg_profile_read() synchronises the
  * stream and returns, for passes 0..CG_NUM_PASSES-1 (streaming of both colours
  * and sums; gradient, normal, curvature, forces and recoloring state;
- * correction term; streaming of the totals and collision), the summed device
+ * correction term and the divergence of R; streaming of the totals and
+ * collision), the summed device
  * time in milliseconds and the number of timed steps. */
 #define CG_NUM_PASSES 4
 int cg_profile_enable(cg_ctx *ctx, int64_t max_steps);

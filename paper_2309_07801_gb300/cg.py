@@ -182,7 +182,7 @@ def cg_profile_read(h):
     return ms, n.value
 
 
-PASS_NAMES = ("k_macro", "k_fields", "k_qcorr", "k_collide")
+PASS_NAMES = ("k_macro", "k_fields", "k_div", "k_collide")
 
 CG_NOALLOC_MAX_CELLS = 67108864
 

@@ -49,7 +49,7 @@ struct Layout {
   long long n = 0, stride = 0;
   size_t elem = 0;      // bytes of an arithmetic value (FP64 or FP32)
   size_t pop_elem = 0;  // bytes of a stored population
-  int ns = 5;           // fields of the recoloring state
+  int ns = 6;           // fields of the recoloring state
   bool solid = false;
   int red_blocks = 0;
   size_t f[2] = {0, 0}, s[2] = {0, 0}, aux[2] = {0, 0};
@@ -100,7 +100,7 @@ Layout make_layout(const cg_params& p) {
   L.stride = (L.n + 63) / 64 * 64;
   L.elem = (p.precision == CG_F64) ? 8 : 4;
   L.pop_elem = (p.precision == CG_F64) ? 8 : (p.precision == CG_F32 ? 4 : 2);
-  L.ns = (p.precision == CG_F16S || p.precision == CG_BF16S) ? 6 : 5;
+  L.ns = (p.precision == CG_F16S || p.precision == CG_BF16S) ? 7 : 6;
   L.solid = needs_solid(p);
   L.red_blocks = (int)std::min<long long>(1024, (L.n + RED_THREADS - 1) / RED_THREADS);
   size_t off = 0;
@@ -237,7 +237,7 @@ void enqueue_step(cg_ctx* c) {
   else
     k_fields<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph, c->tz);
   if (ev) cudaEventRecord(ev[2], c->stream);
-  if (c->prm.use_Q) k_qcorr<T><<<gr, b, 0, c->stream>>>(g, P, c->tz);
+  k_div_sep<T><<<gr, b, 0, c->stream>>>(g, P, c->tz, c->prm.use_Q);
   if (ev) cudaEventRecord(ev[3], c->stream);
   if (c->unit)
     k_collide<T, SF, SOLID, true><<<gc, bc, 0, c->stream>>>(g, P, ph);

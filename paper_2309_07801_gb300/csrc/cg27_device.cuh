@@ -6,11 +6,16 @@
 //   F[27]   post-collision total populations f_i^* (two ping-pong copies);
 //           at solid cells the same slots hold the red part of the stored
 //           (bounced) populations;
-//   S[5]    recoloring state of each cell: rho_r/rho, rho_b/rho, R_x, R_y, R_z
-//           (two ping-pong copies).  The two-colour post-collision
+//   S[6]    recoloring state of each cell: rho_r/rho, rho_b/rho, R_x, R_y, R_z
+//           and DIVR (two ping-pong copies).  The two-colour post-collision
 //           populations of Eq. (recoloring) are f^{r,*}_i = (rho_r/rho) f_i^*
 //           + (w_i/c_s^2) c_i.R and f^{b,*}_i = (rho_b/rho) f_i^* - (w_i/c_s^2)
-//           c_i.R, so (F, S) holds the full two-colour state in 27 + 5 values;
+//           c_i.R, so (F, S) holds the full two-colour state in 27 + 5 values.
+//           DIVR(x) = sum_i (w_i/c_s^2) c_i.R(x - c_i) is what the R terms add
+//           to rho_r (and take from rho_b) after the next pull; it is computed
+//           once per cell by the divergence pass so that the pull needs only
+//           the two fractions of each source cell.  The 16-bit modes add a
+//           seventh field, the rest-direction reference;
 //   AUX[27] blue part at solid cells (only with walls, two copies);
 //   MASK    per cell: bit q set when the neighbour x + c_q is solid, bit 27
 //           when the cell itself is solid (only with walls);
@@ -22,8 +27,8 @@
 //
 // One step is four kernels (cg27_step.cuh): k_macro (pull both colours and
 // sum), k_fields (colour gradient, normal, curvature, forces, velocity,
-// (p - rho c_s^2) u, recoloring state), k_qcorr (correction term Q) and
-// k_collide (pull the totals, CM-MRT collision, store f^*; recoloring is
+// (p - rho c_s^2) u, recoloring state), k_div_sep (correction term Q and DIVR)
+// and k_collide (pull the totals, CM-MRT collision, store f^*; recoloring is
 // applied by the next pull).
 #pragma once
 
@@ -134,7 +139,10 @@ struct Store<__nv_bfloat16> {
 
 // fields of the recoloring state: rho_r/rho, rho_b/rho, R (3) [, rho - p/xi]
 template <typename SF>
-__host__ __device__ constexpr int ns_of() { return Store<SF>::SHIFT ? 6 : 5; }
+__host__ __device__ constexpr int ns_of() { return Store<SF>::SHIFT ? 7 : 6; }
+// fields of the recoloring state after rho_r/rho, rho_b/rho and R
+constexpr int S_DIVR = 5;  // sum over directions of the recoloring term of the source cells
+constexpr int S_REST = 6;  // rest-direction reference of the 16-bit modes
 
 // rest population of the rest direction of a cell
 template <typename T>
@@ -192,7 +200,7 @@ __device__ __forceinline__ void pull_colour(const Ptrs<T>& P, long long stride, 
                                             uint32_t mask, T& fr, T& fb, T& ft, T ph_rest1 = T(0)) {
   static_assert(!(SOLID && Store<SF>::SHIFT), "walls are not available with 16-bit populations");
   T f = Store<SF>::template get<T>(fin<SF>(P.f_in) + q * stride + src);
-  if (Store<SF>::SHIFT) f += q == REST ? ld(P.s_in + 5 * stride + src) : WQ<T>(q) * ph_rest1;
+  if (Store<SF>::SHIFT) f += q == REST ? ld(P.s_in + S_REST * stride + src) : WQ<T>(q) * ph_rest1;
   if (SOLID && ((mask >> OPP(q)) & 1u)) {
     // the source is solid: it stores the red part in F and the blue part in AUX
     fr = f;
@@ -462,7 +470,7 @@ __global__ void __launch_bounds__(128) k_init(Geom g, Ptrs<T> P, Phys<T> ph, con
       fout<SF>(P.f_out)[q * S + i0] = Store<SF>::put(T(0));
       P.aux_out[q * S + i0] = T(0);
     }
-    for (int a = 0; a < 5; ++a) {
+    for (int a = 0; a < 6; ++a) {
       P.s_out[a * S + i0] = T(0);
       P.mac[a * S + i0] = T(0);
     }
@@ -487,7 +495,8 @@ __global__ void __launch_bounds__(128) k_init(Geom g, Ptrs<T> P, Phys<T> ph, con
   P.s_out[i0] = rr / rho;
   P.s_out[S + i0] = rb / rho;
   P.s_out[2 * S + i0] = P.s_out[3 * S + i0] = P.s_out[4 * S + i0] = T(0);
-  if (Store<SF>::SHIFT) P.s_out[5 * S + i0] = r0;
+  P.s_out[S_DIVR * S + i0] = T(0);
+  if (Store<SF>::SHIFT) P.s_out[S_REST * S + i0] = r0;
   P.mac[i0] = rr;
   P.mac[S + i0] = rb;
   for (int a = 0; a < 3; ++a) {
@@ -529,7 +538,7 @@ __global__ void __launch_bounds__(128) k_read_pop(Geom g, Ptrs<T> P, Phys<T> ph,
   const long long S = g.stride;
   const int i0 = c.idx;
   T f = Store<SF>::template get<T>(fin<SF>(P.f_in) + q * S + i0);
-  if (Store<SF>::SHIFT) f += rest_pop(q, P.s_in[5 * S + i0], ph.rest1);
+  if (Store<SF>::SHIFT) f += rest_pop(q, P.s_in[S_REST * S + i0], ph.rest1);
   const bool solid = SOLID && ((ld(P.mask + i0) >> SELF_SOLID_BIT) & 1u);
   if (solid) {
     out_r[i0] = double(f);

@@ -1,4 +1,4 @@
-// cg27_step.cuh -- the three kernels of one time step, as z-marching tiles.
+// cg27_step.cuh -- the four kernels of one time step.
 //
 // k_macro and k_fields run one thread per (x, y) column of a TX x TY tile and
 // walk a range of z planes.  Neighbour data that a stencil reads from the planes
@@ -12,7 +12,8 @@
 //   k_fields  grad phi and n on the tile plus a 1-cell halo, then
 //             kappa, F, u, (p - rho c_s^2) u, R and the recoloring
 //             fractions on the tile                            (Secs. II.A, III.E)
-//   k_qcorr   correction term Q from (p - rho c_s^2) u             (Sec. III.E)
+//   k_div_sep correction term Q from (p - rho c_s^2) u (Sec. III.E) and
+//             the divergence of R that the next pull's colour sums need
 //   k_collide one thread per cell: pull the totals, CM-MRT collision, store
 //             f^*                                           (Secs. II.B, III.E)
 #pragma once
@@ -84,14 +85,14 @@ __device__ __forceinline__ int zoff(const Geom& g, int z) { return wrapi(z, g.nz
 // ---- pass 1 -----------------------------------------------------------------------------
 
 template <typename T, typename SF, bool SOLID>
-__global__ void __launch_bounds__(NT) k_macro(Geom g, Ptrs<T> P, Phys<T> ph, int tz) {
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !SOLID) ? 4 : 1)
+    k_macro(Geom g, Ptrs<T> P, Phys<T> ph, int tz) {
   using HS = HaloSlots<1>;
   constexpr int W = HS::W, PL = HS::PL;
-  constexpr int NS = 5;  // the ring holds what neighbours need
+  constexpr int NS = 2;  // the colour fractions of the source cells
   constexpr bool SHIFT = Store<SF>::SHIFT;
-  // recoloring state of the planes z-1..z+1 (plus the one being prefetched when
-  // FP32 leaves room for a fourth slot), 1-cell halo
-  constexpr int RING = sizeof(T) == 4 ? 4 : 3;
+  // fractions of the planes z-1..z+1 plus the one being loaded, 1-cell halo
+  constexpr int RING = 4;
   __shared__ T sS[RING][NS][PL];
   const Col c = make_col(g);
   const int z0 = blockIdx.z * tz, z1 = min(g.nz, z0 + tz);
@@ -112,63 +113,46 @@ __global__ void __launch_bounds__(NT) k_macro(Geom g, Ptrs<T> P, Phys<T> ph, int
     for (int k = 0; k < HS::K; ++k)
       if (hs.xy[k] >= 0)
 #pragma unroll
-        for (int f = 0; f < NS; ++f) sS[(z + RING) % RING][f][c.tid + k * NT] = pre[k][f];
+        for (int f = 0; f < NS; ++f) sS[z & (RING - 1)][f][c.tid + k * NT] = pre[k][f];
   };
   fetch(z0 - 1);
-  store(z0 - 1);
+  store(z0 - 1 + RING);
   fetch(z0);
-  store(z0);
+  store(z0 + RING);
   fetch(z0 + 1);
-  store(z0 + 1);
+  store(z0 + 1 + RING);
   __syncthreads();
-  // populations of the next plane are loaded while the current one is summed
-  T fn[27];
-  auto fetchf = [&](int z) {
-    if (!c.active) return;
-    const int zo[3] = {zoff(g, z - 1), zoff(g, z), zoff(g, z + 1)};
-#pragma unroll
-    for (int q = 0; q < 27; ++q)
-      fn[q] = Store<SF>::template get<T>(fin<SF>(P.f_in) + q * S +
-                                         (c.xs[1 - CX(q)] + c.ys[1 - CY(q)] + zo[1 - CZ(q)]));
-  };
-  fetchf(z0);
   for (int z = z0; z < z1; ++z) {
     fetch(z + 2);  // in flight while this plane is computed
-    T f[27];
-#pragma unroll
-    for (int q = 0; q < 27; ++q) f[q] = fn[q];
-    if (z + 1 < z1) fetchf(z + 1);
     if (c.active) {
       const int zo[3] = {(z == 0 ? g.nz - 1 : z - 1) * g.nxy, z * g.nxy,
                          (z == g.nz - 1 ? 0 : z + 1) * g.nxy};
       const int i0 = c.xs[1] + c.ys[1] + zo[1];
+      T f[27];
+#pragma unroll
+      for (int q = 0; q < 27; ++q)
+        f[q] = Store<SF>::template get<T>(fin<SF>(P.f_in) + q * S +
+                                          (c.xs[1 - CX(q)] + c.ys[1 - CY(q)] + zo[1 - CZ(q)]));
       const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
-      const T s_rest0 = SHIFT ? ld(P.s_in + 5 * S + i0) : T(0);
-      T rr = T(0), rb = T(0), jx = T(0), jy = T(0), jz = T(0);
+      const T s_rest0 = SHIFT ? ld(P.s_in + S_REST * S + i0) : T(0);
+      // sum over q of (w_q / c_s^2) c_q . R(x - c_q), from the divergence pass
+      const T divr = ld(P.s_in + S_DIVR * S + i0);
+      T rr = divr, rb = -divr, jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
       for (int q = 0; q < 27; ++q) {
         const int src = c.xs[1 - CX(q)] + c.ys[1 - CY(q)] + zo[1 - CZ(q)];
-        const T* s = &sS[(z - CZ(q) + RING) % RING][0][(c.tx + 1 - CX(q)) + W * (c.ty + 1 - CY(q))];
+        const T* s = &sS[(z - CZ(q) + RING) & (RING - 1)][0][(c.tx + 1 - CX(q)) + W * (c.ty + 1 - CY(q))];
         if (SHIFT) f[q] += q == REST ? s_rest0 : WQ<T>(q) * ph.rest1;
-        T fr, fb, ft = f[q];
+        T ft = f[q];
         if (SOLID && ((mask >> OPP(q)) & 1u)) {
-          fr = f[q];
-          fb = ld(P.aux_in + q * S + src);
-          ft = fr + fb;
+          const T fb = ld(P.aux_in + q * S + src);
+          rr += f[q];
+          rb += fb;
+          ft = f[q] + fb;
         } else {
-          T t = T(0);
-          if (q != REST) {
-            T cR = T(0);
-            if (CX(q) != 0) cR += T(CX(q)) * s[2 * PL];
-            if (CY(q) != 0) cR += T(CY(q)) * s[3 * PL];
-            if (CZ(q) != 0) cR += T(CZ(q)) * s[4 * PL];
-            t = (WQ<T>(q) / Lat<T>::CS2) * cR;
-          }
-          fr = s[0] * f[q] + t;
-          fb = s[PL] * f[q] - t;
+          rr += s[0] * f[q];
+          rb += s[PL] * f[q];
         }
-        rr += fr;
-        rb += fb;
         if (CX(q) != 0) jx += T(CX(q)) * ft;
         if (CY(q) != 0) jy += T(CY(q)) * ft;
         if (CZ(q) != 0) jz += T(CZ(q)) * ft;
@@ -182,10 +166,8 @@ __global__ void __launch_bounds__(NT) k_macro(Geom g, Ptrs<T> P, Phys<T> ph, int
       P.phi[i0] = self_solid ? T(0) : order_parameter(rr, rb, ph);
       if (!isfinite(rr + rb)) atomicOr(P.flag, 1u);
     }
-    // with four slots plane z+2 goes to the slot of z-2, last read in the
-    // previous iteration; with three it replaces z-1, read by this one
-    if (RING == 3) __syncthreads();
-    store(z + 2);
+    // plane z+2 goes to the slot of z-2, last read in the previous iteration
+    store(z + 2 + RING);
     __syncthreads();
   }
 }
@@ -356,7 +338,7 @@ __global__ void __launch_bounds__(NT) k_fields(Geom g, Ptrs<T> P, Phys<T> ph, in
         }
         P.s_out[i0] = rr * inv_rho;
         P.s_out[S + i0] = rb * inv_rho;
-        if (ph.shift) P.s_out[5 * S + i0] = rest_zero(rho, p);
+        if (ph.shift) P.s_out[S_REST * S + i0] = rest_zero(rho, p);
       }
     }
     fetch_mac(z + 1);
@@ -531,7 +513,7 @@ __global__ void __launch_bounds__(NT) k_fields_sep(Geom g, Ptrs<T> P, Phys<T> ph
       }
       P.s_out[i0] = rr * inv_rho;
       P.s_out[S + i0] = rb * inv_rho;
-      if (ph.shift) P.s_out[5 * S + i0] = rest_zero(rho, p);
+      if (ph.shift) P.s_out[S_REST * S + i0] = rest_zero(rho, p);
     }
     fetch_mac(z + 1);
     store_phi_ab(z + 3);  // phi z+3 replaces z; A, B of z+2 (own positions)
@@ -539,62 +521,90 @@ __global__ void __launch_bounds__(NT) k_fields_sep(Geom g, Ptrs<T> P, Phys<T> ph
   }
 }
 
-// ---- pass 3: correction term ----------------------------------------------------------
-// Q_a = -3 d_a[(p - rho c_s^2) u_a] with d_a = (1/c_s^2) sum_i w_i c_ia (.)
-// (Sec. III.E); z-marching tile, (p - rho c_s^2) u of planes z-1..z+1 staged in
-// a shared-memory ring.
-
+// ---- pass 3: divergences, separable form ----------------------------------------------
+// With the isotropic difference d_a = D_a S_b S_c (S = (1/6, 2/3, 1/6),
+// D = (-1/2, 0, 1/2), the 1/c_s^2 included):
+//   Q_a = -3 d_a[(p - rho c_s^2) u_a]                     (Sec. III.E), and
+//   sum_q (w_q / c_s^2) c_q . R(x - c_q) = -sum_a d_a R_a, the part of the next
+//   pull's colour sums that comes from the recoloring term of Eq. (recoloring).
+// Each thread keeps both vector fields of planes z-1, z, z+1 at its own halo
+// positions in registers and stages only their z parts (S_z for the in-plane
+// components, D_z for the z component) of the output plane in shared memory
+// (two buffers, one barrier per plane).
 template <typename T>
-__global__ void __launch_bounds__(NT) k_qcorr(Geom g, Ptrs<T> P, int tz) {
+__global__ void __launch_bounds__(NT) k_div_sep(Geom g, Ptrs<T> P, int tz, int use_Q) {
   using HS = HaloSlots<1>;
-  constexpr int W = HS::W, PL = HS::PL;
-  constexpr int RING = sizeof(T) == 4 ? 4 : 3;
-  __shared__ T sW[RING][3][PL];
+  constexpr int W = HS::W, PL = HS::PL, K = HS::K;
+  constexpr T S0 = T(2) / T(3), S1 = T(1) / T(6);
+  __shared__ T sA[2][6][PL];
   const Col c = make_col(g);
   const int z0 = blockIdx.z * tz, z1 = min(g.nz, z0 + tz);
   const long long S = g.stride;
   HS hs;
   hs.init(g, c);
-  T pre[HS::K][3];
-  auto fetch = [&](int z) {
+  // components 0-2: (p - rho c_s^2) u, 3-5: R
+  T lo[K][6], mid[K][6], hi[K][6], nx[K][6];
+  auto fetch = [&](int z, T (&dst)[K][6]) {
     const int zo = zoff(g, z);
 #pragma unroll
-    for (int k = 0; k < HS::K; ++k)
-      if (hs.xy[k] >= 0)
+    for (int k = 0; k < K; ++k)
+      if (hs.xy[k] >= 0) {
 #pragma unroll
-        for (int f = 0; f < 3; ++f) pre[k][f] = ld(P.wv + f * S + hs.xy[k] + zo);
+        for (int f = 0; f < 3; ++f) dst[k][f] = use_Q ? ld(P.wv + f * S + hs.xy[k] + zo) : T(0);
+#pragma unroll
+        for (int f = 0; f < 3; ++f) dst[k][3 + f] = P.s_out[(2 + f) * S + hs.xy[k] + zo];
+      }
   };
-  auto store = [&](int z) {
-#pragma unroll
-    for (int k = 0; k < HS::K; ++k)
-      if (hs.xy[k] >= 0)
-#pragma unroll
-        for (int f = 0; f < 3; ++f) sW[(z + RING) % RING][f][c.tid + k * NT] = pre[k][f];
-  };
-  fetch(z0 - 1); store(z0 - 1);
-  fetch(z0); store(z0);
-  fetch(z0 + 1); store(z0 + 1);
-  __syncthreads();
+  fetch(z0 - 1, lo);
+  fetch(z0, mid);
+  fetch(z0 + 1, hi);
   for (int z = z0; z < z1; ++z) {
-    fetch(z + 2);
+    if (z + 1 < z1) fetch(z + 2, nx);
+    T(*A)[PL] = sA[z & 1];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (hs.xy[k] >= 0) {
+        const int i = c.tid + k * NT;
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          A[3 * v][i] = S1 * (lo[k][3 * v] + hi[k][3 * v]) + S0 * mid[k][3 * v];
+          A[3 * v + 1][i] = S1 * (lo[k][3 * v + 1] + hi[k][3 * v + 1]) + S0 * mid[k][3 * v + 1];
+          A[3 * v + 2][i] = T(0.5) * (hi[k][3 * v + 2] - lo[k][3 * v + 2]);
+        }
+      }
+    __syncthreads();
     if (c.active) {
       const int ctr = (c.tx + 1) + W * (c.ty + 1);
-      T Q[3] = {T(0), T(0), T(0)};
+      T d[2][3];
 #pragma unroll
-      for (int q = 0; q < 27; ++q) {
-        if (q == REST) continue;
-        const int off = ctr + CX(q) + W * CY(q);
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-          if (CA(q, a) != 0) Q[a] += T(CA(q, a)) * (WQ<T>(q) * sW[(z + CZ(q) + RING) % RING][a][off]);
+      for (int v = 0; v < 2; ++v) {
+        const T* Ax = A[3 * v];
+        const T* Ay = A[3 * v + 1];
+        const T* B = A[3 * v + 2];
+        d[v][0] = T(0.5) * (S1 * (Ax[ctr + 1 - W] - Ax[ctr - 1 - W]) + S0 * (Ax[ctr + 1] - Ax[ctr - 1]) +
+                            S1 * (Ax[ctr + 1 + W] - Ax[ctr - 1 + W]));
+        d[v][1] = T(0.5) * (S1 * (Ay[ctr - 1 + W] - Ay[ctr - 1 - W]) + S0 * (Ay[ctr + W] - Ay[ctr - W]) +
+                            S1 * (Ay[ctr + 1 + W] - Ay[ctr + 1 - W]));
+        d[v][2] = S1 * (S1 * B[ctr - 1 - W] + S0 * B[ctr - W] + S1 * B[ctr + 1 - W]) +
+                  S0 * (S1 * B[ctr - 1] + S0 * B[ctr] + S1 * B[ctr + 1]) +
+                  S1 * (S1 * B[ctr - 1 + W] + S0 * B[ctr + W] + S1 * B[ctr + 1 + W]);
       }
       const int i0 = c.xs[1] + c.ys[1] + z * g.nxy;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) P.qc[a * S + i0] = T(-9) * Q[a];
+      if (use_Q) {
+        P.qc[i0] = T(-3) * d[0][0];
+        P.qc[S + i0] = T(-3) * d[0][1];
+        P.qc[2 * S + i0] = T(-3) * d[0][2];
+      }
+      P.s_out[S_DIVR * S + i0] = -(d[1][0] + d[1][1] + d[1][2]);
     }
-    if (RING == 3) __syncthreads();
-    store(z + 2);
-    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        lo[k][f] = mid[k][f];
+        mid[k][f] = hi[k][f];
+        hi[k][f] = nx[k][f];
+      }
   }
 }
 
@@ -629,7 +639,7 @@ __global__ void __launch_bounds__(128, 6) k_collide(Geom g, Ptrs<T> P, Phys<T> p
   for (int q = 0; q < 27; ++q)
     f[q] = Store<SF>::template get<T>(fin<SF>(P.f_in) + q * S + nbr(c, -CX(q), -CY(q), -CZ(q)));
   if (SHIFT) {
-    const T r0 = ld(P.s_in + 5 * S + i0);
+    const T r0 = ld(P.s_in + S_REST * S + i0);
 #pragma unroll
     for (int q = 0; q < 27; ++q) f[q] += rest_pop(q, r0, ph.rest1);
   }
@@ -664,7 +674,7 @@ __global__ void __launch_bounds__(128, 6) k_collide(Geom g, Ptrs<T> P, Phys<T> p
   for (int a = 0; a < 3; ++a) u[a] = (j[a] + T(0.5) * F[a]) * inv_rho;
   collide_cm<T, UNIT>(f, rho, p, u[0], u[1], u[2], F, Q, om1, ph);
   // the rest-direction shift is the value the field pass stored for this cell
-  const T r0n = SHIFT ? P.s_out[5 * S + i0] : T(0);
+  const T r0n = SHIFT ? P.s_out[S_REST * S + i0] : T(0);
 #pragma unroll
   for (int q = 0; q < 27; ++q)
     fout<SF>(P.f_out)[q * S + i0] = Store<SF>::put(SHIFT ? f[q] - rest_pop(q, r0n, ph.rest1) : f[q]);

@@ -11,6 +11,13 @@ domains only, so there is no collective on the data path; scaling is weak).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The line also carries a serving measurement ("serving"): 256 independent static
+or oscillating droplet runs (edges 32..128, ratio 1..10, 500..5000 steps) with
+Poisson arrivals, admitted by free device memory and advanced together in
+shared launches (continuous batching); it reports p50/p99 time to result,
+runs per hour and the aggregate MLUPS.  --serve-compare adds the same requests
+arriving at once, served batched and with one set of launches per run.
+
 The reference arm times the FP64 CPU oracle as it stands on the host cores, on
 a bounded periodic slab of the same workload per step.
 """
@@ -46,6 +53,12 @@ def parse_args():
     ap.add_argument("--edge", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--serve-rate", type=float, default=3.8,
+                    help="Poisson arrivals per second (about 0.8 of the batched capacity)")
+    ap.add_argument("--serve-compare", action="store_true",
+                    help="also serve all requests arriving at once, batched and per run")
     return ap.parse_args()
 
 
@@ -342,16 +355,50 @@ def run_ours(args, dist):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": describe(wl), "cells": N,
                        "parallelism": "replicas" if dist.world > 1 else "single",
-                       "l2": "inputs larger than L2: population state 2 x %.0f MB" %
-                             (N * 128 / 1e6)},
+                       "l2": "inputs larger than L2: populations and recoloring state 2 x %.0f MB" %
+                             (N * (27 + 6) * 4 / 1e6)},
             "roofline": roofline, "step_roofline_432B": step_roofline,
             "e2e": e2e, "gpu_launches": len(cg.PASS_NAMES) * K, "clocks": clk,
             "mass": list(map(float, mass)), "nonfinite": nonfinite}
+    if not args.no_serve:
+        line["serving"] = serving(args)
     if not args.no_cpu_baseline and dist.world == 1:
         line["cpu_baseline"] = cpu_baseline(args.edge, args.cpu_budget)
     elif not args.no_cpu_baseline:
         line["cpu_baseline"] = None
     print(json.dumps(line), flush=True)
+
+
+def _serve(mode, reqs):
+    from paper_2309_07801_gb300 import serve
+    srv = serve.Server(mode=mode, precision="f32")
+    res = srv.run(reqs)
+    srv.close()
+    res.pop("results")
+    return {k: res[k] for k in ("mode", "runs", "wall_s", "p50_s", "p99_s", "runs_per_h", "MLUPS",
+                                "max_active", "nonfinite_runs")}
+
+
+def serving(args):
+    """Continuous batching of independent runs (see paper_2309_07801_gb300/serve.py)."""
+    from paper_2309_07801_gb300 import inputs
+    warm = inputs.serving_requests(n=2, rate=1000.0, seed=5)
+    for r in warm:
+        r.steps = 20
+    _serve("batched", warm)
+    reqs = inputs.serving_requests(n=args.serve_requests, rate=args.serve_rate, seed=4)
+    out = {"workload": "%d static/oscillating droplet runs, edge in {32,48,64,96,128}, R/edge in "
+                       "[0.2,0.35], ratio in [1,10], sigma in [0.001,0.02], 500-5000 steps, "
+                       "Poisson arrivals %.2f/s, FP32, admitted by free HBM" %
+                       (args.serve_requests, args.serve_rate),
+           "cell_updates": int(sum(r.cells * r.steps for r in reqs)),
+           "poisson": _serve("batched", reqs)}
+    if args.serve_compare:
+        burst = inputs.serving_requests(n=args.serve_requests, rate=1e9, seed=4)
+        out["burst_batched"] = _serve("batched", burst)
+        _serve("per_run", warm)
+        out["burst_per_run"] = _serve("per_run", burst)
+    return out
 
 
 def main():

@@ -190,8 +190,70 @@ int cg_profile_read(cg_ctx *ctx, double ms[CG_NUM_PASSES], int64_t *steps);
 int cg_mass_noalloc(const void *d_rho_r, const void *d_rho_b, int64_t n,
                     int32_t precision, void *cuda_stream, double out_mass[2]);
 
-/* Release the domain (the workspace stays the caller's). */
+/* Release the domain (the workspace stays the caller's).  A member of a batch
+ * must be removed from it first (CG_ERR_INVALID_ARG otherwise). */
 int cg_destroy(cg_ctx *ctx);
+
+/* ---- batches: many domains advanced in shared launches -------------------
+ * The paper has no counterpart: this is the library's way of running many
+ * independent simulations (different sizes and parameters) at once.  A batch
+ * step advances every member domain by one time step with four launches in
+ * total: each pass runs over a work list that concatenates the tiles of all
+ * members, with the arithmetic of cg_step() for every cell, so each member's
+ * results are bitwise those of stepping it alone.  The four launches are
+ * captured into CUDA graphs (per step parity) and replayed; the z depth of
+ * the tiles is tuned online by timing three depths on the first steps after
+ * the member set has changed by more than a factor two in cells (those steps
+ * are ordinary steps: results do not depend on the depth).
+ *
+ * Members must share the batch's precision and kernel variant (walls or none;
+ * unit-rate Model D or not), else CG_ERR_UNSUPPORTED.  While a domain is a
+ * member, cg_step(), cg_init_fields(), cg_load_state() and cg_destroy() on it
+ * fail with CG_ERR_INVALID_ARG; the read calls (cg_read_macros,
+ * cg_read_populations, cg_reduce, cg_save_state) first wait for the batch's
+ * stream.  cg_steps_taken() counts batch steps too. */
+typedef struct cg_batch cg_batch;
+
+/* Device bytes of the descriptor table and work lists of a batch of up to
+ * max_domains members (1 <= max_domains <= 2^20) of the given precision. */
+int cg_batch_workspace_bytes(int32_t max_domains, int32_t precision, size_t *bytes);
+
+/* Create an empty batch.  d_workspace: device pointer of at least
+ * cg_batch_workspace_bytes() bytes, 256-byte aligned, owned by the caller and
+ * kept alive until cg_batch_destroy().  cuda_stream: the stream all batch
+ * launches go to (NULL = legacy default stream, which cannot be captured:
+ * plain launches are used then). */
+int cg_batch_create(int32_t max_domains, int32_t precision, void *d_workspace, size_t bytes,
+                    void *cuda_stream, cg_batch **out);
+
+/* Add an initialised domain (synchronises the domain's own stream first).
+ * Fails with CG_ERR_INVALID_ARG when the batch is full or the domain is
+ * already a member of a batch. */
+int cg_batch_add(cg_batch *batch, cg_ctx *ctx);
+
+/* Remove a member (synchronises the batch stream first). */
+int cg_batch_remove(cg_batch *batch, cg_ctx *ctx);
+
+/* Number of members. */
+int cg_batch_size(cg_batch *batch, int32_t *n);
+
+/* Enqueue nsteps batch steps on the batch stream.  Returns without waiting,
+ * except while the depth is being tuned (the tuned steps are timed with
+ * events and synchronised). */
+int cg_batch_step(cg_batch *batch, int64_t nsteps);
+
+/* Wait for all enqueued batch steps. */
+int cg_batch_sync(cg_batch *batch);
+
+/* Fix the z depth of the tiles (planes per tile, > 0), or 0 to tune it
+ * online again. */
+int cg_batch_set_depth(cg_batch *batch, int32_t tz);
+
+/* Current depth (0 before the first step) and whether tuning is under way. */
+int cg_batch_depth(cg_batch *batch, int32_t *tz, int32_t *tuning);
+
+/* Release the batch (waits for its stream; members become free domains). */
+int cg_batch_destroy(cg_batch *batch);
 
 /* Text of the last error on the calling thread ("" if none). */
 const char *cg_last_error(void);

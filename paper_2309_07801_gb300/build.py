@@ -13,8 +13,8 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libcg27.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--shared",
-         "-Xptxas", "-O3"]
+COMPILE = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-O3"]
+FLAGS = COMPILE + ["--shared"]  # one-step build of a variant (sources and link together)
 
 
 def nvcc() -> str:
@@ -38,14 +38,32 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every CUDA source into one shared library (no-op when fresh)."""
+    """Compile every CUDA source (in parallel, one object each) and link them
+    into one shared library (no-op when fresh)."""
     if not (force or _stale()):
         return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc()] + ARCH + FLAGS + ["-I" + INCLUDE, "-I" + CSRC, "-o", tmp] + sources()
+    objdir = os.path.join(PKG, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    tag = "%d" % os.getpid()
+    procs = []
+    objs = []
+    for src in sources():
+        obj = os.path.join(objdir, os.path.basename(src) + "." + tag + ".o")
+        cmd = [nvcc()] + ARCH + COMPILE + ["-I" + INCLUDE, "-I" + CSRC, "-c", "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd))
+        procs.append((subprocess.Popen(cmd, cwd=PKG), src))
+        objs.append(obj)
+    failed = [src for p, src in procs if p.wait() != 0]
+    if failed:
+        raise RuntimeError("nvcc failed on " + ", ".join(failed))
+    tmp = LIB + ".tmp" + tag
+    cmd = [nvcc()] + ARCH + ["--shared", "-o", tmp] + objs
     if verbose:
         print(" ".join(cmd))
     subprocess.check_call(cmd, cwd=PKG)
+    for o in objs:
+        os.remove(o)
     os.replace(tmp, LIB)
     return LIB
 

@@ -67,6 +67,17 @@ SIGNATURES = {
     "cg_destroy": (ctypes.c_int, [_VP]),
     "cg_last_error": (ctypes.c_char_p, []),
     "cg_abi_version": (ctypes.c_int, []),
+    "cg_batch_workspace_bytes": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+    "cg_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _VP, ctypes.c_size_t, _VP,
+                                       ctypes.POINTER(_VP)]),
+    "cg_batch_add": (ctypes.c_int, [_VP, _VP]),
+    "cg_batch_remove": (ctypes.c_int, [_VP, _VP]),
+    "cg_batch_size": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32)]),
+    "cg_batch_step": (ctypes.c_int, [_VP, ctypes.c_int64]),
+    "cg_batch_sync": (ctypes.c_int, [_VP]),
+    "cg_batch_set_depth": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "cg_batch_depth": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "cg_batch_destroy": (ctypes.c_int, [_VP])
 }
 
 _lib = None
@@ -288,3 +299,107 @@ class Domain:
     @property
     def steps(self) -> int:
         return cg_steps_taken(self.h)
+
+
+# ---- batches --------------------------------------------------------------------------------
+
+def cg_batch_workspace_bytes(max_domains: int, precision) -> int:
+    n = ctypes.c_size_t(0)
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check(lib().cg_batch_workspace_bytes(int(max_domains), prec, ctypes.byref(n)))
+    return n.value
+
+
+def cg_batch_create(max_domains: int, precision, d_ws: int, nbytes: int, stream: int):
+    out = _VP()
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check(lib().cg_batch_create(int(max_domains), prec, ctypes.c_void_p(d_ws), nbytes,
+                                 ctypes.c_void_p(stream), ctypes.byref(out)))
+    return out
+
+
+def cg_batch_add(b, h):
+    _check(lib().cg_batch_add(b, h))
+
+
+def cg_batch_remove(b, h):
+    _check(lib().cg_batch_remove(b, h))
+
+
+def cg_batch_size(b) -> int:
+    n = ctypes.c_int32(0)
+    _check(lib().cg_batch_size(b, ctypes.byref(n)))
+    return n.value
+
+
+def cg_batch_step(b, nsteps: int):
+    _check(lib().cg_batch_step(b, int(nsteps)))
+
+
+def cg_batch_sync(b):
+    _check(lib().cg_batch_sync(b))
+
+
+def cg_batch_set_depth(b, tz: int):
+    _check(lib().cg_batch_set_depth(b, int(tz)))
+
+
+def cg_batch_depth(b):
+    tz, tuning = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(lib().cg_batch_depth(b, ctypes.byref(tz), ctypes.byref(tuning)))
+    return tz.value, bool(tuning.value)
+
+
+def cg_batch_destroy(b):
+    _check(lib().cg_batch_destroy(b))
+
+
+class Batch:
+    """Domains advanced together in shared launches (see cg_batch_* in the C
+    header).  The descriptor workspace is a uint8 CUDA tensor; launches go to a
+    torch CUDA stream (a new one unless given)."""
+
+    def __init__(self, max_domains: int, precision="f32", device="cuda", stream=None):
+        import torch
+        self.nbytes = cg_batch_workspace_bytes(max_domains, precision)
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.workspace.device)
+        self.h = cg_batch_create(max_domains, precision, self.workspace.data_ptr(), self.nbytes,
+                                 self.stream.cuda_stream)
+        self.members = []
+
+    def add(self, dom: Domain):
+        cg_batch_add(self.h, dom.h)
+        self.members.append(dom)
+
+    def remove(self, dom: Domain):
+        cg_batch_remove(self.h, dom.h)
+        self.members.remove(dom)
+
+    def step(self, n: int = 1):
+        cg_batch_step(self.h, n)
+
+    def sync(self):
+        cg_batch_sync(self.h)
+
+    def set_depth(self, tz: int):
+        cg_batch_set_depth(self.h, tz)
+
+    @property
+    def depth(self):
+        return cg_batch_depth(self.h)
+
+    def __len__(self):
+        return cg_batch_size(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            cg_batch_destroy(self.h)
+            self.h = None
+            self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

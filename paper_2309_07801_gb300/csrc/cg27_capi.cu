@@ -1,9 +1,7 @@
 // cg27_capi.cu -- host side of the C ABI declared in include/cg27.h:
 // workspace layout, kernel launches of one time step, initialisation,
 // read-back, reductions and checkpoints.  Device code is in cg27_device.cuh.
-#include "cg27.h"
-#include "cg27_device.cuh"
-#include "cg27_step.cuh"
+#include "cg27_host.cuh"
 
 #include <cmath>
 #include <cstdio>
@@ -14,23 +12,6 @@
 using namespace cg27;
 
 namespace {
-
-thread_local std::string g_err;
-
-int fail(int code, const std::string& msg) {
-  g_err = msg;
-  return code;
-}
-
-#define CG_CUDA(expr)                                                              \
-  do {                                                                             \
-    cudaError_t e_ = (expr);                                                       \
-    if (e_ != cudaSuccess)                                                         \
-      return fail(CG_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
-  } while (0)
-
-constexpr size_t ALIGN = 256;
-size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 // paper velocity order (Sec. II.A) -> lexicographic storage index
 int paper_to_lex(int i) {
@@ -45,17 +26,12 @@ int paper_to_lex(int i) {
 constexpr int RED_THREADS = 256;
 constexpr int NUM_EVENTS_PER_STEP = CG_NUM_PASSES + 1;
 
-struct Layout {
-  long long n = 0, stride = 0;
-  size_t elem = 0;      // bytes of an arithmetic value (FP64 or FP32)
-  size_t pop_elem = 0;  // bytes of a stored population
-  int ns = 6;           // fields of the recoloring state
-  bool solid = false;
-  int red_blocks = 0;
-  size_t f[2] = {0, 0}, s[2] = {0, 0}, aux[2] = {0, 0};
-  size_t mask = 0, mac = 0, phi = 0, qc = 0, force = 0, wv = 0;
-  size_t partial = 0, flag = 0, result = 0, total = 0;
-};
+// steps a batch has enqueued for a member domain complete before the
+// domain's own stream reads its state
+int settle(const cg_ctx* c) {
+  if (c->batch) CG_CUDA(cudaStreamSynchronize(c->batch_stream));
+  return CG_OK;
+}
 
 bool needs_solid(const cg_params& p) {
   return p.solid_mask != 0 || p.bc[0] == CG_BC_BOUNCEBACK || p.bc[1] == CG_BC_BOUNCEBACK ||
@@ -133,87 +109,9 @@ dim3 block_of(const cg_params& p) {
   return dim3(bx, 128 / bx, 1);
 }
 
-}  // namespace
-
-struct cg_ctx {
-  cg_params prm;
-  Layout L;
-  char* ws = nullptr;
-  cudaStream_t stream = nullptr;
-  int64_t steps = 0;
-  bool initialised = false;
-  bool unit = false;  // all omega = 1 except omega_1, Model D: the Sec. III.E form
-  int tz = 1;         // z planes per tile of the step kernels
-  // per-pass timing: events[NUM_EVENTS_PER_STEP * s + k] brackets pass k of timed step s
-  std::vector<cudaEvent_t> events;
-  int64_t prof_capacity = 0, prof_used = 0;
-  ~cg_ctx() {
-    for (cudaEvent_t e : events) cudaEventDestroy(e);
-  }
-};
-
-namespace {
-
-template <typename T>
-Phys<T> make_phys(const cg_params& p) {
-  Phys<T> ph;
-  const double xi = 9.0 / 19.0;
-  ph.rho_r0 = T(p.rho_r0);
-  ph.rho_b0 = T(p.rho_b0);
-  ph.inv_rho_r0 = T(1.0 / p.rho_r0);
-  ph.inv_rho_b0 = T(1.0 / p.rho_b0);
-  ph.cr2 = T(xi * (1.0 - p.alpha_r));
-  ph.cb2 = T(xi * (1.0 - p.alpha_b));
-  ph.nu_r = T(p.nu_r);
-  ph.nu_b = T(p.nu_b);
-  ph.sigma = T(p.sigma);
-  ph.beta = T(p.beta);
-  for (int q = 0; q < 11; ++q) ph.om[q] = T(p.omega[q]);
-  for (int a = 0; a < 3; ++a) ph.g[a] = T(p.g[a]);
-  ph.rho_ref = T(p.rho_ref);
-  ph.force_mode = p.force_mode;
-  ph.model = p.model;
-  ph.use_Q = p.use_Q;
-  ph.shift = (p.precision == CG_F16S || p.precision == CG_BF16S) ? 1 : 0;
-  // reference pressure of the red phase at its reference density
-  ph.rest1 = T(3.0 * p.rho_r0 * xi * (1.0 - p.alpha_r));
-  return ph;
-}
-
-Geom make_geom(const cg_ctx* c) {
-  Geom g;
-  g.nx = c->prm.nx;
-  g.ny = c->prm.ny;
-  g.nz = c->prm.nz;
-  g.nxy = c->prm.nx * c->prm.ny;
-  g.stride = c->L.stride;
-  return g;
-}
 
 dim3 grid_of(const cg_params& p, dim3 b) {
   return dim3((p.nx + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, p.nz);
-}
-
-// pointers for a step that reads buffer `cur` and writes buffer 1 - cur
-template <typename T>
-Ptrs<T> make_ptrs(const cg_ctx* c, int cur) {
-  const Layout& L = c->L;
-  Ptrs<T> P;
-  char* w = c->ws;
-  P.f_in = w + L.f[cur];
-  P.f_out = w + L.f[1 - cur];
-  P.s_in = reinterpret_cast<const T*>(w + L.s[cur]);
-  P.s_out = reinterpret_cast<T*>(w + L.s[1 - cur]);
-  P.aux_in = L.solid ? reinterpret_cast<const T*>(w + L.aux[cur]) : nullptr;
-  P.aux_out = L.solid ? reinterpret_cast<T*>(w + L.aux[1 - cur]) : nullptr;
-  P.mask = L.solid ? reinterpret_cast<const uint32_t*>(w + L.mask) : nullptr;
-  P.mac = reinterpret_cast<T*>(w + L.mac);
-  P.phi = reinterpret_cast<T*>(w + L.phi);
-  P.qc = reinterpret_cast<T*>(w + L.qc);
-  P.force = reinterpret_cast<T*>(w + L.force);
-  P.wv = reinterpret_cast<T*>(w + L.wv);
-  P.flag = reinterpret_cast<unsigned int*>(w + L.flag);
-  return P;
 }
 
 template <typename T, typename SF, bool SOLID>
@@ -400,6 +298,7 @@ int cg_create(const cg_params* p, void* d_workspace, size_t bytes, void* cuda_st
 }
 
 int cg_destroy(cg_ctx* c) {
+  if (c && c->batch) return fail(CG_ERR_INVALID_ARG, "the domain is a member of a batch: remove it first");
   delete c;
   return CG_OK;
 }
@@ -407,6 +306,7 @@ int cg_destroy(cg_ctx* c) {
 int cg_init_fields(cg_ctx* c, const double* rho_r, const double* rho_b, const double* u,
                    const uint8_t* solid) {
   if (!c) return fail(CG_ERR_INVALID_ARG, "ctx is NULL");
+  if (c->batch) return fail(CG_ERR_INVALID_ARG, "the domain is a member of a batch: remove it first");
   if (!rho_r || !rho_b || !u) return fail(CG_ERR_INVALID_ARG, "rho_r, rho_b, u must be non-NULL");
   if (solid && !c->L.solid)
     return fail(CG_ERR_INVALID_ARG, "a solid mask needs params.solid_mask = 1 or a bounce-back axis");
@@ -452,6 +352,7 @@ int cg_init_fields(cg_ctx* c, const double* rho_r, const double* rho_b, const do
 
 int cg_step(cg_ctx* c, int64_t nsteps) {
   if (!c) return fail(CG_ERR_INVALID_ARG, "ctx is NULL");
+  if (c->batch) return fail(CG_ERR_INVALID_ARG, "the domain is a member of a batch: remove it first");
   if (!c->initialised) return fail(CG_ERR_INVALID_ARG, "cg_init_fields() has not been called");
   if (nsteps < 0) return fail(CG_ERR_INVALID_ARG, "nsteps must be >= 0");
   for (int64_t s = 0; s < nsteps; ++s) {
@@ -464,6 +365,7 @@ int cg_step(cg_ctx* c, int64_t nsteps) {
 
 int cg_read_macros(cg_ctx* c, double* rho_r, double* rho_b, double* u, double* p, double* phi) {
   if (!c) return fail(CG_ERR_INVALID_ARG, "ctx is NULL");
+  if (int rc_ = settle(c)) return rc_;
   if (!c->initialised) return fail(CG_ERR_INVALID_ARG, "cg_init_fields() has not been called");
   const long long n = c->L.n;
   double* d_out = reinterpret_cast<double*>(scratch_of(c));
@@ -492,6 +394,7 @@ int cg_read_macros(cg_ctx* c, double* rho_r, double* rho_b, double* u, double* p
 
 int cg_read_populations(cg_ctx* c, double* fr, double* fb) {
   if (!c) return fail(CG_ERR_INVALID_ARG, "ctx is NULL");
+  if (int rc_ = settle(c)) return rc_;
   if (!c->initialised) return fail(CG_ERR_INVALID_ARG, "cg_init_fields() has not been called");
   const long long n = c->L.n;
   double* d_out = reinterpret_cast<double*>(scratch_of(c));
@@ -527,6 +430,7 @@ int cg_read_populations(cg_ctx* c, double* fr, double* fb) {
 
 int cg_reduce(cg_ctx* c, double out_mass[2], int32_t* nonfinite) {
   if (!c) return fail(CG_ERR_INVALID_ARG, "ctx is NULL");
+  if (int rc_ = settle(c)) return rc_;
   if (!c->initialised) return fail(CG_ERR_INVALID_ARG, "cg_init_fields() has not been called");
   const Geom g = make_geom(c);
   double* partial = reinterpret_cast<double*>(c->ws + c->L.partial);
@@ -629,6 +533,7 @@ int cg_state_bytes(cg_ctx* c, size_t* bytes) {
 
 int cg_save_state(cg_ctx* c, void* host, size_t bytes) {
   if (!c || !host) return fail(CG_ERR_INVALID_ARG, "NULL argument");
+  if (int rc_ = settle(c)) return rc_;
   if (!c->initialised) return fail(CG_ERR_INVALID_ARG, "cg_init_fields() has not been called");
   size_t need = 0;
   cg_state_bytes(c, &need);
@@ -656,6 +561,7 @@ int cg_save_state(cg_ctx* c, void* host, size_t bytes) {
 
 int cg_load_state(cg_ctx* c, const void* host, size_t bytes) {
   if (!c || !host) return fail(CG_ERR_INVALID_ARG, "NULL argument");
+  if (c->batch) return fail(CG_ERR_INVALID_ARG, "the domain is a member of a batch: remove it first");
   if (bytes < sizeof(StateHeader)) return fail(CG_ERR_INVALID_ARG, "buffer too small");
   StateHeader h;
   std::memcpy(&h, host, sizeof(h));

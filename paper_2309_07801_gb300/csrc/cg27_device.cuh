@@ -167,11 +167,8 @@ struct Cell {
   int xs[3], ys[3], zs[3];  // offsets of x-1, x, x+1 (etc.) with periodic wrap
 };
 
-__device__ __forceinline__ bool make_cell(const Geom& g, Cell& c) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  if (x >= g.nx || y >= g.ny) return false;
+// the cell (x, y, z), which must lie inside the domain
+__device__ __forceinline__ void make_cell_at(const Geom& g, int x, int y, int z, Cell& c) {
   c.xs[0] = (x == 0 ? g.nx - 1 : x - 1);
   c.xs[1] = x;
   c.xs[2] = (x == g.nx - 1 ? 0 : x + 1);
@@ -182,6 +179,14 @@ __device__ __forceinline__ bool make_cell(const Geom& g, Cell& c) {
   c.zs[1] = z * g.nxy;
   c.zs[2] = (z == g.nz - 1 ? 0 : z + 1) * g.nxy;
   c.idx = x + c.ys[1] + c.zs[1];
+}
+
+// the cell of this thread in a (x, y) block grid with one z plane per blockIdx.z
+__device__ __forceinline__ bool make_cell(const Geom& g, Cell& c) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return false;
+  make_cell_at(g, x, y, blockIdx.z, c);
   return true;
 }
 

@@ -1,0 +1,125 @@
+// cg27_host.cuh -- host-side state shared by the C-ABI translation units:
+// the error text, the workspace layout of a domain, the domain context and the
+// kernel argument builders.  Internal to the library (not installed).
+#pragma once
+
+#include "cg27.h"
+#include "cg27_device.cuh"
+#include "cg27_step.cuh"
+
+#include <string>
+#include <vector>
+
+namespace cg27 {
+
+inline thread_local std::string g_err;
+
+inline int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CG_CUDA(expr)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (expr);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(CG_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr size_t ALIGN = 256;
+inline size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Layout {
+  long long n = 0, stride = 0;
+  size_t elem = 0;      // bytes of an arithmetic value (FP64 or FP32)
+  size_t pop_elem = 0;  // bytes of a stored population
+  int ns = 6;           // fields of the recoloring state
+  bool solid = false;
+  int red_blocks = 0;
+  size_t f[2] = {0, 0}, s[2] = {0, 0}, aux[2] = {0, 0};
+  size_t mask = 0, mac = 0, phi = 0, qc = 0, force = 0, wv = 0;
+  size_t partial = 0, flag = 0, result = 0, total = 0;
+};
+
+}  // namespace cg27
+
+struct cg_ctx {
+  cg_params prm;
+  cg_batch* batch = nullptr;  // the batch the domain is a member of, if any
+  cudaStream_t batch_stream = nullptr;  // and the stream that batch launches on
+  cg27::Layout L;
+  char* ws = nullptr;
+  cudaStream_t stream = nullptr;
+  int64_t steps = 0;
+  bool initialised = false;
+  bool unit = false;  // all omega = 1 except omega_1, Model D: the Sec. III.E form
+  int tz = 1;         // z planes per tile of the step kernels
+  // per-pass timing: events[(CG_NUM_PASSES + 1) * s + k] brackets pass k of timed step s
+  std::vector<cudaEvent_t> events;
+  int64_t prof_capacity = 0, prof_used = 0;
+  ~cg_ctx() {
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+  }
+};
+
+namespace cg27 {
+
+template <typename T>
+inline Phys<T> make_phys(const cg_params& p) {
+  Phys<T> ph;
+  const double xi = 9.0 / 19.0;
+  ph.rho_r0 = T(p.rho_r0);
+  ph.rho_b0 = T(p.rho_b0);
+  ph.inv_rho_r0 = T(1.0 / p.rho_r0);
+  ph.inv_rho_b0 = T(1.0 / p.rho_b0);
+  ph.cr2 = T(xi * (1.0 - p.alpha_r));
+  ph.cb2 = T(xi * (1.0 - p.alpha_b));
+  ph.nu_r = T(p.nu_r);
+  ph.nu_b = T(p.nu_b);
+  ph.sigma = T(p.sigma);
+  ph.beta = T(p.beta);
+  for (int q = 0; q < 11; ++q) ph.om[q] = T(p.omega[q]);
+  for (int a = 0; a < 3; ++a) ph.g[a] = T(p.g[a]);
+  ph.rho_ref = T(p.rho_ref);
+  ph.force_mode = p.force_mode;
+  ph.model = p.model;
+  ph.use_Q = p.use_Q;
+  ph.shift = (p.precision == CG_F16S || p.precision == CG_BF16S) ? 1 : 0;
+  // reference pressure of the red phase at its reference density
+  ph.rest1 = T(3.0 * p.rho_r0 * xi * (1.0 - p.alpha_r));
+  return ph;
+}
+
+inline Geom make_geom(const cg_ctx* c) {
+  Geom g;
+  g.nx = c->prm.nx;
+  g.ny = c->prm.ny;
+  g.nz = c->prm.nz;
+  g.nxy = c->prm.nx * c->prm.ny;
+  g.stride = c->L.stride;
+  return g;
+}
+
+// pointers for a step that reads buffer `cur` and writes buffer 1 - cur
+template <typename T>
+inline Ptrs<T> make_ptrs(const cg_ctx* c, int cur) {
+  const Layout& L = c->L;
+  Ptrs<T> P;
+  char* w = c->ws;
+  P.f_in = w + L.f[cur];
+  P.f_out = w + L.f[1 - cur];
+  P.s_in = reinterpret_cast<const T*>(w + L.s[cur]);
+  P.s_out = reinterpret_cast<T*>(w + L.s[1 - cur]);
+  P.aux_in = L.solid ? reinterpret_cast<const T*>(w + L.aux[cur]) : nullptr;
+  P.aux_out = L.solid ? reinterpret_cast<T*>(w + L.aux[1 - cur]) : nullptr;
+  P.mask = L.solid ? reinterpret_cast<const uint32_t*>(w + L.mask) : nullptr;
+  P.mac = reinterpret_cast<T*>(w + L.mac);
+  P.phi = reinterpret_cast<T*>(w + L.phi);
+  P.qc = reinterpret_cast<T*>(w + L.qc);
+  P.force = reinterpret_cast<T*>(w + L.force);
+  P.wv = reinterpret_cast<T*>(w + L.wv);
+  P.flag = reinterpret_cast<unsigned int*>(w + L.flag);
+  return P;
+}
+
+}  // namespace cg27

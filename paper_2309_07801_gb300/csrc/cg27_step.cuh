@@ -38,13 +38,13 @@ struct Col {
   int ys[3];   // (y-1, y, y+1) * nx (wrapped)
 };
 
-__device__ __forceinline__ Col make_col(const Geom& g) {
+__device__ __forceinline__ Col make_col(const Geom& g, int bx, int by) {
   Col c;
   c.tx = threadIdx.x;
   c.ty = threadIdx.y;
   c.tid = c.tx + TX * c.ty;
-  c.x0 = blockIdx.x * TX;
-  c.y0 = blockIdx.y * TY;
+  c.x0 = bx * TX;
+  c.y0 = by * TY;
   const int x = c.x0 + c.tx, y = c.y0 + c.ty;
   c.active = x < g.nx && y < g.ny;
   const int xx = c.active ? x : 0, yy = c.active ? y : 0;
@@ -85,8 +85,8 @@ __device__ __forceinline__ int zoff(const Geom& g, int z) { return wrapi(z, g.nz
 // ---- pass 1 -----------------------------------------------------------------------------
 
 template <typename T, typename SF, bool SOLID>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !SOLID) ? 4 : 1)
-    k_macro(Geom g, Ptrs<T> P, Phys<T> ph, int tz) {
+__device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, const Phys<T>& ph, int tz,
+                                           int bx, int by, int bz) {
   using HS = HaloSlots<1>;
   constexpr int W = HS::W, PL = HS::PL;
   constexpr int NS = 2;  // the colour fractions of the source cells
@@ -94,8 +94,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !SOLID) ? 4 : 1)
   // fractions of the planes z-1..z+1 plus the one being loaded, 1-cell halo
   constexpr int RING = 4;
   __shared__ T sS[RING][NS][PL];
-  const Col c = make_col(g);
-  const int z0 = blockIdx.z * tz, z1 = min(g.nz, z0 + tz);
+  const Col c = make_col(g, bx, by);
+  const int z0 = bz * tz, z1 = min(g.nz, z0 + tz);
   const long long S = g.stride;
   HS hs;
   hs.init(g, c);
@@ -175,15 +175,16 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !SOLID) ? 4 : 1)
 // ---- pass 2 -----------------------------------------------------------------------------
 
 template <typename T, bool SOLID>
-__global__ void __launch_bounds__(NT) k_fields(Geom g, Ptrs<T> P, Phys<T> ph, int tz) {
+__device__ __forceinline__ void fields_tile(const Geom& g, const Ptrs<T>& P, const Phys<T>& ph, int tz,
+                                            int bx, int by, int bz) {
   using H2 = HaloSlots<2>;  // phi, 2-cell halo
   using H1 = HaloSlots<1>;  // n, 1-cell halo
   constexpr int W2 = H2::W, P2 = H2::PL, W1 = H1::W, P1 = H1::PL;
   __shared__ T sPhi[3][P2];  // phi of three planes (ring3)
   __shared__ T sN[3][3][P1];  // n of three planes (ring3)
   __shared__ T sG[2][3][NT];  // grad phi of the tile cells, planes of parity 0 and 1
-  const Col c = make_col(g);
-  const int z0 = blockIdx.z * tz, z1 = min(g.nz, z0 + tz);
+  const Col c = make_col(g, bx, by);
+  const int z0 = bz * tz, z1 = min(g.nz, z0 + tz);
   const long long S = g.stride;
   H2 h2;
   h2.init(g, c);
@@ -357,7 +358,8 @@ __global__ void __launch_bounds__(NT) k_fields(Geom g, Ptrs<T> P, Phys<T> ph, in
 // thread stages A, B for exactly the positions it loaded or computed itself, so
 // no extra barrier is needed.
 template <typename T>
-__global__ void __launch_bounds__(NT) k_fields_sep(Geom g, Ptrs<T> P, Phys<T> ph, int tz) {
+__device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P, const Phys<T>& ph, int tz,
+                                                int bx, int by, int bz) {
   using H2 = HaloSlots<2>;
   using H1 = HaloSlots<1>;
   constexpr int W2 = H2::W, P2 = H2::PL, W1 = H1::W, P1 = H1::PL;
@@ -367,8 +369,8 @@ __global__ void __launch_bounds__(NT) k_fields_sep(Geom g, Ptrs<T> P, Phys<T> ph
   __shared__ T sN[3][3][P1];
   __shared__ T sNA[3][P1], sNB[3][P1];  // S_z n_b and D_z n_b of the output plane
   __shared__ T sG[2][3][NT];
-  const Col c = make_col(g);
-  const int z0 = blockIdx.z * tz, z1 = min(g.nz, z0 + tz);
+  const Col c = make_col(g, bx, by);
+  const int z0 = bz * tz, z1 = min(g.nz, z0 + tz);
   const long long S = g.stride;
   H2 h2;
   h2.init(g, c);
@@ -532,13 +534,14 @@ __global__ void __launch_bounds__(NT) k_fields_sep(Geom g, Ptrs<T> P, Phys<T> ph
 // components, D_z for the z component) of the output plane in shared memory
 // (two buffers, one barrier per plane).
 template <typename T>
-__global__ void __launch_bounds__(NT) k_div_sep(Geom g, Ptrs<T> P, int tz, int use_Q) {
+__device__ __forceinline__ void div_sep_tile(const Geom& g, const Ptrs<T>& P, int tz, int use_Q, int bx, int by,
+                                             int bz) {
   using HS = HaloSlots<1>;
   constexpr int W = HS::W, PL = HS::PL, K = HS::K;
   constexpr T S0 = T(2) / T(3), S1 = T(1) / T(6);
   __shared__ T sA[2][6][PL];
-  const Col c = make_col(g);
-  const int z0 = blockIdx.z * tz, z1 = min(g.nz, z0 + tz);
+  const Col c = make_col(g, bx, by);
+  const int z0 = bz * tz, z1 = min(g.nz, z0 + tz);
   const long long S = g.stride;
   HS hs;
   hs.init(g, c);
@@ -615,10 +618,8 @@ __global__ void __launch_bounds__(NT) k_div_sep(Geom g, Ptrs<T> P, int tz, int u
 // this occupancy the kernel streams at about the copy bandwidth of the device.
 
 template <typename T, typename SF, bool SOLID, bool UNIT>
-__global__ void __launch_bounds__(128, 6) k_collide(Geom g, Ptrs<T> P, Phys<T> ph) {
+__device__ __forceinline__ void collide_cell(const Geom& g, const Ptrs<T>& P, const Phys<T>& ph, const Cell& c) {
   constexpr bool SHIFT = Store<SF>::SHIFT;
-  Cell c;
-  if (!make_cell(g, c)) return;
   const long long S = g.stride;
   const int i0 = c.idx;
   const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
@@ -678,6 +679,111 @@ __global__ void __launch_bounds__(128, 6) k_collide(Geom g, Ptrs<T> P, Phys<T> p
 #pragma unroll
   for (int q = 0; q < 27; ++q)
     fout<SF>(P.f_out)[q * S + i0] = Store<SF>::put(SHIFT ? f[q] - rest_pop(q, r0n, ph.rest1) : f[q]);
+}
+
+// ---- kernels of one domain ------------------------------------------------------------------
+// Grid (tiles in x, tiles in y, z chunks of tz planes) of TX x TY blocks for the
+// z-marching passes; one thread per cell, one z plane per blockIdx.z, for the
+// collision.
+
+template <typename T, typename SF, bool SOLID>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !SOLID) ? 4 : 1)
+    k_macro(Geom g, Ptrs<T> P, Phys<T> ph, int tz) {
+  macro_tile<T, SF, SOLID>(g, P, ph, tz, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+template <typename T, bool SOLID>
+__global__ void __launch_bounds__(NT) k_fields(Geom g, Ptrs<T> P, Phys<T> ph, int tz) {
+  fields_tile<T, SOLID>(g, P, ph, tz, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_fields_sep(Geom g, Ptrs<T> P, Phys<T> ph, int tz) {
+  fields_sep_tile<T>(g, P, ph, tz, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_div_sep(Geom g, Ptrs<T> P, int tz, int use_Q) {
+  div_sep_tile<T>(g, P, tz, use_Q, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+template <typename T, typename SF, bool SOLID, bool UNIT>
+__global__ void __launch_bounds__(128, 6) k_collide(Geom g, Ptrs<T> P, Phys<T> ph) {
+  Cell c;
+  if (!make_cell(g, c)) return;
+  collide_cell<T, SF, SOLID, UNIT>(g, P, ph, c);
+}
+
+// ---- kernels of a batch of domains -----------------------------------------------------------
+// Every pass of every member domain is one launch over a work list: block b of
+// a z-marching pass reads its item (domain, tile x, tile y, z chunk) from a
+// table written on the host, so a block starts from one 16-byte load; block b
+// of the collision covers cells 128 (b - cell_start[d]) ... + 127 of the
+// domain d with cell_start[d] <= b < cell_start[d + 1], in storage order.  The
+// arithmetic of each cell is that of the single-domain kernels.
+
+template <typename T>
+struct Dom {
+  Geom g;
+  Phys<T> ph;
+  Ptrs<T> P[2];  // buffers of the even and odd steps of the batch
+  int tz, tiles_x, tiles_y, use_Q;
+};
+
+// largest d with start[d] <= b (start is non-decreasing, start[0] = 0)
+__device__ __forceinline__ int find_domain(const int* __restrict__ start, int ndom, int b) {
+  int lo = 0, hi = ndom - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// one z-marching tile of a batch: domain, tile x, tile y, z chunk
+__device__ __forceinline__ int4 tile_item(const int4* __restrict__ items) { return __ldg(items + blockIdx.x); }
+
+template <typename T, typename SF, bool SOLID>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !SOLID) ? 4 : 1)
+    k_macro_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int par) {
+  const int4 t = tile_item(items);
+  const Dom<T>& D = doms[t.x];
+  macro_tile<T, SF, SOLID>(D.g, D.P[par], D.ph, D.tz, t.y, t.z, t.w);
+}
+
+template <typename T, bool SOLID>
+__global__ void __launch_bounds__(NT)
+    k_fields_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int par) {
+  const int4 t = tile_item(items);
+  const Dom<T>& D = doms[t.x];
+  if constexpr (!SOLID && sizeof(T) == 4)
+    fields_sep_tile<T>(D.g, D.P[par], D.ph, D.tz, t.y, t.z, t.w);
+  else
+    fields_tile<T, SOLID>(D.g, D.P[par], D.ph, D.tz, t.y, t.z, t.w);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT)
+    k_div_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int par) {
+  const int4 t = tile_item(items);
+  const Dom<T>& D = doms[t.x];
+  div_sep_tile<T>(D.g, D.P[par], D.tz, D.use_Q, t.y, t.z, t.w);
+}
+
+template <typename T, typename SF, bool SOLID, bool UNIT>
+__global__ void __launch_bounds__(128, 6)
+    k_collide_batch(const Dom<T>* __restrict__ doms, const int* __restrict__ start, int ndom, int par) {
+  const int d = find_domain(start, ndom, blockIdx.x);
+  const Dom<T>& D = doms[d];
+  // domains hold fewer than 2^31 cells, so 32-bit unsigned index arithmetic is exact
+  const unsigned i = (unsigned)(blockIdx.x - __ldg(start + d)) * 128u + threadIdx.x;
+  const unsigned nxy = (unsigned)D.g.nxy, nx = (unsigned)D.g.nx;
+  if (i >= nxy * (unsigned)D.g.nz) return;
+  const unsigned z = i / nxy, r = i - z * nxy, y = r / nx;
+  Cell c;
+  make_cell_at(D.g, (int)(r - y * nx), (int)y, (int)z, c);
+  collide_cell<T, SF, SOLID, UNIT>(D.g, D.P[par], D.ph, c);
 }
 
 }  // namespace cg27

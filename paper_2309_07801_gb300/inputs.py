@@ -195,3 +195,60 @@ def workload_fields(wl: Workload, seed: int = 0, noise: float = 0.0):
     if wl.name.startswith("droplet_collision"):
         return collision_fields(wl)
     raise ValueError("unknown workload " + wl.name)
+
+
+# ---- serving workload: many independent droplet runs -------------------------------------
+
+SERVING_EDGES = (32, 48, 64, 96, 128)
+
+
+@dataclass
+class Request:
+    """One independent simulation request (a static or oscillating droplet in a
+    periodic cube): arrival time in seconds after the start of the run."""
+    rid: int
+    arrival: float
+    edge: int
+    radius: float
+    ratio: float
+    sigma: float
+    steps: int
+    kind: str  # "static" (sphere) or "oscillating" (ellipsoid, equal volume)
+
+    @property
+    def cells(self) -> int:
+        return self.edge ** 3
+
+    def workload(self) -> Workload:
+        ar, ab = rest_fractions(1.0, 1.0 / self.ratio)
+        return Workload(self.edge, self.edge, self.edge, rho_r0=1.0, rho_b0=1.0 / self.ratio,
+                        alpha_r=ar, alpha_b=ab, nu_r=0.1, nu_b=0.1, sigma=self.sigma, beta=0.7,
+                        steps=self.steps, name="serving_%s_%d" % (self.kind, self.rid))
+
+    def fields(self):
+        n = self.edge
+        c = (n / 2.0, n / 2.0, n / 2.0)
+        semi = None
+        if self.kind == "oscillating":
+            R = self.radius
+            semi = (R * 1.1, R * 0.95, R * 0.95)
+        return droplet_fields((n, n, n), c, self.radius, 1.0, 1.0 / self.ratio, semi_axes=semi)
+
+
+def serving_requests(n: int = 256, rate: float = 4.0, seed: int = 4):
+    """n requests with Poisson arrivals at `rate` per second: edge uniform in
+    {32, 48, 64, 96, 128}, radius uniform in [0.2, 0.35] edge, density ratio
+    uniform in [1, 10], sigma uniform in [0.001, 0.02], steps uniform in
+    500..5000, half static spheres and half oscillating ellipsoids."""
+    u = splitmix64(seed, 8 * n).reshape(n, 8)
+    out, t = [], 0.0
+    for i in range(n):
+        t += -math.log(1.0 - float(u[i, 0])) / rate
+        out.append(Request(
+            rid=i, arrival=t,
+            edge=SERVING_EDGES[min(4, int(u[i, 1] * 5))],
+            radius=0.0, ratio=float(1.0 + 9.0 * u[i, 3]), sigma=float(0.001 + 0.019 * u[i, 4]),
+            steps=500 + min(4500, int(u[i, 5] * 4501)),
+            kind="static" if u[i, 6] < 0.5 else "oscillating"))
+        out[-1].radius = float((0.2 + 0.15 * u[i, 2]) * out[-1].edge)
+    return out

@@ -1,0 +1,168 @@
+"""Continuous-batching server for many independent colour-gradient runs.
+
+Requests (a droplet problem, a step count, an arrival time) are admitted while
+device memory and batch slots allow; every admitted run keeps its state on the
+device and all active runs advance together.  In the "batched" mode one batch
+step is four shared launches over the tiles of every active run (cg_batch_*,
+replayed from CUDA graphs); in the "per_run" mode each run is stepped with its
+own launches (cg_step), one run after the other, on the same stream.  Runs
+finish at different times; a finished run is read back (per-colour mass,
+pressure jump, largest velocity, non-finite flag) and its memory goes to the
+next arrivals.  Time to result is measured from a request's arrival to the end
+of its read-back on the host clock.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+from . import cg
+
+
+@dataclass
+class Result:
+    rid: int
+    edge: int
+    steps: int
+    arrival: float
+    admitted: float
+    finished: float
+    mass0: np.ndarray
+    mass: np.ndarray
+    dp: float
+    u_max: float
+    nonfinite: int
+    macros: Optional[dict] = None
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+@dataclass
+class _Run:
+    req: object
+    dom: cg.Domain
+    done: int
+    admitted: float
+    mass0: np.ndarray
+
+
+def _summary(req, dom: cg.Domain, keep_macros: bool):
+    m = dom.macros()
+    mass, flag = dom.mass()
+    n = req.edge
+    c = n / 2.0
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    r = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2)
+    inner, outer = r < 0.5 * req.radius, r > req.radius + 0.25 * n
+    dp = float(m["p"][inner].mean() - m["p"][outer].mean()) if inner.any() and outer.any() else float("nan")
+    return mass, float(dp), float(np.abs(m["u"]).max()), flag, (m if keep_macros else None)
+
+
+class Server:
+    """mode: "batched" (shared launches) or "per_run" (one run's launches at a
+    time).  hbm_budget: bytes of workspace the active runs may hold (default:
+    80 % of the device memory); max_active: batch slots; quantum: most steps
+    advanced between admission checks."""
+
+    def __init__(self, mode="batched", precision="f32", max_active=256, quantum=100,
+                 hbm_budget: Optional[int] = None, device="cuda", keep_macros=False, depth=0):
+        import torch
+        if mode not in ("batched", "per_run"):
+            raise ValueError("mode must be 'batched' or 'per_run'")
+        self.mode, self.precision, self.quantum = mode, precision, int(quantum)
+        self.max_active, self.keep_macros = int(max_active), keep_macros
+        self.device = torch.device(device)
+        total = torch.cuda.get_device_properties(self.device).total_memory
+        self.hbm_budget = int(0.8 * total) if hbm_budget is None else int(hbm_budget)
+        self.stream = torch.cuda.Stream(self.device)
+        self.batch = None
+        if mode == "batched":
+            self.batch = cg.Batch(self.max_active, precision, device=self.device, stream=self.stream)
+            if depth:
+                self.batch.set_depth(depth)
+        self.log: List[tuple] = []
+
+    def close(self):
+        if self.batch is not None:
+            self.batch.close()
+            self.batch = None
+
+    def _admit(self, req, now) -> _Run:
+        wl = req.workload()
+        dom = cg.Domain(cg.make_params(precision=self.precision, **wl.params()), device=self.device,
+                        stream=self.stream)
+        dom.init(*req.fields())
+        mass0, _ = dom.mass()
+        if self.batch is not None:
+            self.batch.add(dom)
+        return _Run(req, dom, 0, now, mass0)
+
+    def run(self, requests, clock=time.perf_counter) -> dict:
+        import torch
+        pending = sorted(requests, key=lambda r: r.arrival)
+        active: List[_Run] = []
+        results: List[Result] = []
+        used = 0
+        cell_updates = 0
+        t0 = clock()
+        i = 0
+        while i < len(pending) or active:
+            now = clock() - t0
+            # admission: arrived, a slot free, and the workspace fits the budget
+            while i < len(pending) and pending[i].arrival <= now and len(active) < self.max_active:
+                need = cg.cg_workspace_bytes(cg.make_params(precision=self.precision,
+                                                            **pending[i].workload().params()))
+                if used + need > self.hbm_budget:
+                    break
+                active.append(self._admit(pending[i], now))
+                used += need
+                i += 1
+                now = clock() - t0
+            if not active:
+                if i < len(pending):
+                    time.sleep(max(0.0, min(0.05, pending[i].arrival - (clock() - t0))))
+                continue
+            k = min(self.quantum, min(r.req.steps - r.done for r in active))
+            if self.batch is not None:
+                self.batch.step(k)
+                self.batch.sync()
+            else:
+                for r in active:
+                    r.dom.step(k)
+                self.stream.synchronize()
+            for r in active:
+                r.done += k
+                cell_updates += k * r.req.cells
+            self.log.append((clock() - t0, len(active), k))
+            for r in [r for r in active if r.done >= r.req.steps]:
+                if self.batch is not None:
+                    self.batch.remove(r.dom)
+                mass, dp, umax, flag, mac = _summary(r.req, r.dom, self.keep_macros)
+                fin = clock() - t0
+                results.append(Result(r.req.rid, r.req.edge, r.req.steps, r.req.arrival, r.admitted, fin,
+                                      r.mass0, mass, dp, umax, flag, mac))
+                active.remove(r)
+                used -= r.dom.nbytes
+                r.dom.close()
+                del r.dom
+        wall = clock() - t0
+        lat = np.array([r.latency for r in results])
+        return {
+            "mode": self.mode,
+            "runs": len(results),
+            "wall_s": wall,
+            "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+            "runs_per_h": 3600.0 * len(results) / wall if wall > 0 else None,
+            "MLUPS": cell_updates / wall / 1e6 if wall > 0 else None,
+            "cell_updates": cell_updates,
+            "max_active": max((a for _, a, _ in self.log), default=0),
+            "nonfinite_runs": int(sum(1 for r in results if r.nonfinite)),
+            "results": results,
+        }

@@ -75,7 +75,7 @@ def load_peaks():
 def source_sha():
     import hashlib
     h = hashlib.sha256()
-    for name in ("cg27_device.cuh", "cg27_step.cuh", "cg27_capi.cu"):
+    for name in ("cg27_device.cuh", "cg27_step.cuh", "cg27_host.cuh", "cg27_capi.cu"):
         with open(os.path.join(ROOT, "paper_2309_07801_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -73,7 +73,8 @@ extern "C" {
 #define CG_F32 1   /* FP32 storage and arithmetic */
 #define CG_F16S 2  /* populations stored in FP16 as deviations from the cell's
                       rest-state populations (the equilibrium at u = 0 of
-                      Sec. II.A); everything else FP32; periodic domains only */
+                      Sec. II.A); everything else FP32; periodic domains of
+                      at most 159 million cells (27 * cells < 2^32) only */
 #define CG_BF16S 3 /* as CG_F16S with BF16 storage */
 
 typedef struct cg_params {

@@ -66,6 +66,9 @@ int validate(const cg_params* p) {
     return fail(CG_ERR_UNSUPPORTED, "precision must be CG_F64, CG_F32, CG_F16S or CG_BF16S");
   if ((p->precision == CG_F16S || p->precision == CG_BF16S) && needs_solid(*p))
     return fail(CG_ERR_UNSUPPORTED, "walls are not available with 16-bit population storage");
+  if ((p->precision == CG_F16S || p->precision == CG_BF16S) &&
+      27.0 * (((double)p->nx * p->ny * p->nz + 63) / 64 * 64) >= 4294967296.0)
+    return fail(CG_ERR_UNSUPPORTED, "16-bit population storage is limited to 159 million cells");
   if (p->reserved_ != 0) return fail(CG_ERR_INVALID_ARG, "reserved_ must be 0");
   return CG_OK;
 }

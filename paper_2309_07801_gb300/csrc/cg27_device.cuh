@@ -105,12 +105,13 @@ struct Phys {
 
 // ---- population storage ---------------------------------------------------------------
 // FP64/FP32 store f_q itself.  The 16-bit modes store the deviation of f_q from
-// a rest-state population, the equilibrium at u = 0 of Sec. II.A:
+// a rest-state population (the equilibrium at u = 0 of Sec. II.A), divided by
+// the lattice weight w_q (pop_encode / pop_decode below):
 //   moving directions:  w_q p / c_s^2 with a global reference pressure p_ref
 //                       (pressure balance keeps p close to p_ref in both
 //                       phases, so no per-cell value has to travel);
 //   rest direction:     rho - p / xi of the cell itself, stored in FP32 as
-//                       field 5 of the recoloring state (the rest population
+//                       field S_REST of the recoloring state (the rest population
 //                       stays in its cell, so only the cell's own value is read).
 template <typename SF>
 struct Store {
@@ -149,10 +150,20 @@ template <typename T>
 __device__ __forceinline__ T rest_zero(T rho, T p) {
   return rho - p * (T(19) / T(9));  // 1/xi, xi = 9/19 for D3Q27
 }
-// rest-state population of direction q (r0: the cell's rest_zero)
-template <typename T>
-__device__ __forceinline__ T rest_pop(int q, T r0, T rest1) {
-  return q == REST ? r0 : WQ<T>(q) * rest1;
+
+// 16-bit modes: the stored value is the deviation from the rest-state
+// population divided by the lattice weight, (f_q - rest_q) / w_q, so that all
+// directions use the same range of the format (the corner directions' small
+// deviations stay out of the FP16 subnormals); one FMA each way.
+template <bool SHIFT, typename T>
+__device__ __forceinline__ T pop_decode(int q, T s, T r0, T rest1) {
+  if (!SHIFT) return s;
+  return s * WQ<T>(q) + (q == REST ? r0 : WQ<T>(q) * rest1);
+}
+template <bool SHIFT, typename T>
+__device__ __forceinline__ T pop_encode(int q, T f, T r0, T rest1) {
+  if (!SHIFT) return f;
+  return q == REST ? (f - r0) * (T(1) / WQ<T>(q)) : f * (T(1) / WQ<T>(q)) - rest1;
 }
 
 template <typename SF>
@@ -205,7 +216,8 @@ __device__ __forceinline__ void pull_colour(const Ptrs<T>& P, long long stride, 
                                             uint32_t mask, T& fr, T& fb, T& ft, T ph_rest1 = T(0)) {
   static_assert(!(SOLID && Store<SF>::SHIFT), "walls are not available with 16-bit populations");
   T f = Store<SF>::template get<T>(fin<SF>(P.f_in) + q * stride + src);
-  if (Store<SF>::SHIFT) f += q == REST ? ld(P.s_in + S_REST * stride + src) : WQ<T>(q) * ph_rest1;
+  if (Store<SF>::SHIFT)
+    f = pop_decode<true>(q, f, q == REST ? ld(P.s_in + S_REST * stride + src) : T(0), ph_rest1);
   if (SOLID && ((mask >> OPP(q)) & 1u)) {
     // the source is solid: it stores the red part in F and the blue part in AUX
     fr = f;
@@ -494,7 +506,7 @@ __global__ void __launch_bounds__(128) k_init(Geom g, Ptrs<T> P, Phys<T> ph, con
 #pragma unroll
   for (int q = 0; q < 27; ++q)
     fout<SF>(P.f_out)[q * S + i0] =
-        Store<SF>::put(Store<SF>::SHIFT ? k[q] - rest_pop(q, r0, ph.rest1) : k[q]);
+        Store<SF>::put(pop_encode<Store<SF>::SHIFT>(q, k[q], r0, ph.rest1));
   if (SOLID)
     for (int q = 0; q < 27; ++q) P.aux_out[q * S + i0] = T(0);
   P.s_out[i0] = rr / rho;
@@ -543,7 +555,7 @@ __global__ void __launch_bounds__(128) k_read_pop(Geom g, Ptrs<T> P, Phys<T> ph,
   const long long S = g.stride;
   const int i0 = c.idx;
   T f = Store<SF>::template get<T>(fin<SF>(P.f_in) + q * S + i0);
-  if (Store<SF>::SHIFT) f += rest_pop(q, P.s_in[S_REST * S + i0], ph.rest1);
+  if (Store<SF>::SHIFT) f = pop_decode<true>(q, f, P.s_in[S_REST * S + i0], ph.rest1);
   const bool solid = SOLID && ((ld(P.mask + i0) >> SELF_SOLID_BIT) & 1u);
   if (solid) {
     out_r[i0] = double(f);

@@ -151,6 +151,22 @@ def rising_bubble(nx=192, ny=192, nz=384) -> Workload:
                     steps=20000, name="rising_bubble_%dx%dx%d" % (nx, ny, nz))
 
 
+def rising_bubble_case2(nx=192, ny=192, nz=384) -> Workload:
+    """Case 2 of the bubble test of Sec. IV.D (ratio 1000, viscosity ratio 100,
+    Eo = 125, Re = 35, liquid Mach number 0.0548) in 3D with R = nx / 8 = 24:
+    U = sqrt(g D) = 1e-3 lattice units, g = U^2 / D, sigma = rho_l g D^2 / Eo,
+    nu_l = U D / Re, nu_g = 10 nu_l (dynamic ratio 100); z walls, buoyancy form."""
+    ar, ab = rest_fractions(1.0, 0.001)
+    D = nx / 4.0
+    U = 1e-3
+    g = U * U / D
+    nu_l = U * D / 35.0
+    return Workload(nx, ny, nz, bc=(0, 0, 1), rho_r0=1.0, rho_b0=0.001,
+                    alpha_r=ar, alpha_b=ab, nu_r=nu_l, nu_b=10.0 * nu_l,
+                    sigma=g * D * D / 125.0, beta=0.2, g=(0.0, 0.0, -g), rho_ref=1.0,
+                    force_mode=3, steps=20000, name="rising_bubble_case2_%dx%dx%d" % (nx, ny, nz))
+
+
 def droplet_collision(edge=512) -> Workload:
     """Head-on binary collision: two droplets of radius 48/512 edge closing at a
     relative speed 0.2 along x, ratio 1, nu = 0.002, sigma = 0.005."""

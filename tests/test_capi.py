@@ -104,3 +104,15 @@ def test_walls_rejected_with_16_bit_storage(cg, prec):
     with pytest.raises(cg.CGError) as e:
         cg.cg_workspace_bytes(p)
     assert e.value.code == -2
+
+
+def test_16_bit_storage_size_limit(cg):
+    """27 x cells must stay below 2^32 with 16-bit populations (32-bit indices)."""
+    p = cg.make_params(540, 540, 540, precision="f16s")
+    assert cg.cg_workspace_bytes(p) > 0
+    p = cg.make_params(600, 600, 600, precision="bf16s")
+    with pytest.raises(cg.CGError) as e:
+        cg.cg_workspace_bytes(p)
+    assert e.value.code == -2
+    p.precision = cg.CG_F32
+    assert cg.cg_workspace_bytes(p) > 0

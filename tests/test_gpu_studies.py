@@ -1,0 +1,50 @@
+"""Configuration studies on the GPU against stored oracle values.
+
+The translating droplet (64^3 copy of the 128^3 workload, ratio 10, 4000
+steps): red-mass centroid and shape distortion every 500 steps against the
+FP64 oracle run stored in tests/golden/translating_droplet_64_oracle.txt
+(written by make_translating_droplet_64.py, which calls only the oracle and
+computes the diagnostics with its own code)."""
+import numpy as np
+import pytest
+
+from conftest import load_golden
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2309_07801_gb300 import build, cg
+    build.build()
+    cg.lib()
+
+
+def _golden():
+    rows = load_golden("translating_droplet_64_oracle.txt")
+    return {int(r[0]): (np.array([float(r[1]), float(r[2]), float(r[3])]), float(r[4]),
+                        np.array([float(r[5]), float(r[6])])) for r in rows}
+
+
+# centroid (cells), shape distortion (absolute), per-colour mass (relative)
+BARS = {"f64": (1e-9, 1e-9, 1e-12), "f32": (5e-3, 1e-4, 1e-6)}
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_translating_droplet_64_against_oracle(prec):
+    from paper_2309_07801_gb300 import studies
+    gold = _golden()
+    run = studies.translating(64, 4000, 500, prec)
+    bc, bs, bm = BARS[prec]
+    m0 = gold[0][2]
+    for s in run["samples"]:
+        assert not s["nonfinite"]
+        cen, shape, mass = gold[s["step"]]
+        assert np.abs(np.array(s["centroid"]) - cen).max() <= bc, (s["step"], s["centroid"], cen)
+        assert abs(s["shape"] - shape) <= bs, (s["step"], s["shape"], shape)
+        assert np.all(np.array(s["mass_drift"]) <= bm + np.abs(mass - m0) / m0)
+    # the oracle's own Galilean-invariance error: the droplet lags u0 t by about 5 %
+    last = run["samples"][-1]
+    assert -12.0 < last["drift"][0] < -8.0 and abs(last["drift"][2]) < 1e-3

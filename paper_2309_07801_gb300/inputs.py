@@ -167,6 +167,33 @@ def rising_bubble_case2(nx=192, ny=192, nz=384) -> Workload:
                     force_mode=3, steps=20000, name="rising_bubble_case2_%dx%dx%d" % (nx, ny, nz))
 
 
+def rayleigh_taylor(W=128, Re=1024.0, model=3) -> Workload:
+    """Sec. IV.E: W x W x 4W fluid layers between no-slip walls (two more solid
+    z layers), heavy red (rho 1) over light blue (rho 1/3, Atwood 0.5),
+    sqrt(W g) = 0.04, Re = sqrt(W g) W / nu, equal kinematic viscosities, no
+    interfacial tension, F = (rho - (rho_r0 + rho_b0)/2) g with g = (0, 0, -g)."""
+    ar, ab = rest_fractions(1.0, 1.0 / 3.0)
+    g = 0.04 ** 2 / W
+    nu = 0.04 * W / Re
+    return Workload(W, W, 4 * W + 2, bc=(0, 0, 1), rho_r0=1.0, rho_b0=1.0 / 3.0, alpha_r=ar, alpha_b=ab,
+                    nu_r=nu, nu_b=nu, sigma=0.0, beta=0.7, g=(0.0, 0.0, -g), rho_ref=(1.0 + 1.0 / 3.0) / 2.0,
+                    force_mode=3, model=model, steps=int(3 * math.sqrt(W / g)),
+                    name="rayleigh_taylor_%d_Re%g" % (W, Re))
+
+
+def rayleigh_taylor_fields(wl: Workload, width=4.0):
+    """Interface at the middle of the fluid layers displaced by
+    h(x, y) = 0.05 W [cos(2 pi x / W) + cos(2 pi y / W)]; heavy fluid above."""
+    W = wl.nx
+    z, y, x = np.meshgrid(np.arange(wl.nz), np.arange(wl.ny), np.arange(wl.nx), indexing="ij")
+    z_mid = (wl.nz - 1) / 2.0
+    h = 0.05 * W * (np.cos(2.0 * math.pi * x / W) + np.cos(2.0 * math.pi * y / W))
+    phi0 = np.tanh(2.0 * (z - (z_mid + h)) / width)
+    rho_r = wl.rho_r0 * (1.0 + phi0) / 2.0
+    rho_b = wl.rho_b0 * (1.0 - phi0) / 2.0
+    return rho_r, rho_b, np.zeros((3,) + rho_r.shape)
+
+
 def droplet_collision(edge=512) -> Workload:
     """Head-on binary collision: two droplets of radius 48/512 edge closing at a
     relative speed 0.2 along x, ratio 1, nu = 0.002, sigma = 0.005."""
@@ -210,6 +237,8 @@ def workload_fields(wl: Workload, seed: int = 0, noise: float = 0.0):
                               noise=noise, seed=seed, invert=True)
     if wl.name.startswith("droplet_collision"):
         return collision_fields(wl)
+    if wl.name.startswith("rayleigh_taylor"):
+        return rayleigh_taylor_fields(wl)
     raise ValueError("unknown workload " + wl.name)
 
 

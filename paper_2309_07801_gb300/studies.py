@@ -8,13 +8,16 @@
       z_c = sum rho_b z / sum rho_b and velocity V_c = sum rho_b u_z / sum rho_b
       (the definitions of Sec. IV.D), per-colour mass drift;
   head-on droplet collision: per-colour mass drift and the fraction of
-      interface cells whose phi has the other sign than in a reference run.
+      interface cells whose phi has the other sign than in a reference run;
+  Rayleigh-Taylor instability (Sec. IV.E): heights of the bubble, saddle and
+      spike points of the phi = 0 surface against T = t / sqrt(W / g).
 
 Everything here runs through the CUDA library; the CPU oracle is not used.
 
     python -m paper_2309_07801_gb300.studies translating --edge 128 --steps 4000 --every 500
     python -m paper_2309_07801_gb300.studies bubble --steps 20000 --every 2000 --precisions f32,f64
     python -m paper_2309_07801_gb300.studies collision --edge 512 --steps 10000 --every 2000
+    python -m paper_2309_07801_gb300.studies rti --edge 128 --steps 9600 --every 800 --model D
 """
 from __future__ import annotations
 
@@ -144,6 +147,45 @@ def bubble(steps=20000, every=2000, precision="f32", nx=192, ny=192, nz=384, cas
             "wall_s": wall, "samples": rows}
 
 
+def interface_height(phi_col: np.ndarray) -> float:
+    """z where phi crosses 0 along a vertical line (heavy fluid, phi > 0, above);
+    the crossing closest to the middle, linear interpolation."""
+    s = np.sign(phi_col)
+    idx = np.nonzero(s[:-1] * s[1:] < 0)[0]
+    if len(idx) == 0:
+        return float("nan")
+    mid = (len(phi_col) - 1) / 2.0
+    k = idx[np.argmin(np.abs(idx - mid))]
+    a, b = phi_col[k], phi_col[k + 1]
+    return float(k + a / (a - b))
+
+
+def rti(W=128, steps=None, every=None, precision="f32", model=3, Re=1024.0):
+    """Rayleigh-Taylor instability (Sec. IV.E): heights of the bubble (x = y = 0),
+    saddle (x = 0, y = W/2) and spike (x = y = W/2) relative to the initial
+    mid-plane, in units of W, against T = t / sqrt(W / g)."""
+    wl = inputs.rayleigh_taylor(W, Re, model)
+    fields = inputs.workload_fields(wl)
+    g = -wl.g[2]
+    t_unit = math.sqrt(W / g)
+    steps = wl.steps if steps is None else steps
+    every = int(round(0.25 * t_unit)) if every is None else every
+    z_mid = (wl.nz - 1) / 2.0
+    points = {"bubble": (0, 0), "saddle": (0, W // 2), "spike": (W // 2, W // 2)}
+
+    def sample(step, d):
+        m = d.macros()
+        mass, flag = d.mass()
+        row = {"step": step, "T": step / t_unit, "nonfinite": flag}
+        for name, (x, y) in points.items():
+            row[name] = (interface_height(m["phi"][:, y, x]) - z_mid) / W
+        return row
+
+    rows, wall = run_series(wl, fields, precision, steps, every, sample)
+    return {"study": "rti", "W": W, "Re": Re, "model": "ABCD"[model], "precision": precision, "steps": steps,
+            "wall_s": wall, "MLUPS": wl.cells * steps / wall / 1e6, "samples": rows}
+
+
 def collision(edge=512, steps=10000, every=2000, precisions=("f64", "f32", "f16s", "bf16s")):
     """All precisions side by side; the first one is the reference for phi."""
     wl = inputs.droplet_collision(edge)
@@ -175,7 +217,8 @@ def collision(edge=512, steps=10000, every=2000, precisions=("f64", "f32", "f16s
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["translating", "bubble", "collision"])
+    ap.add_argument("study", choices=["translating", "bubble", "collision", "rti"])
+    ap.add_argument("--model", default="D", choices=["A", "B", "C", "D"])
     ap.add_argument("--edge", type=int, default=128)
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--every", type=int, default=500)
@@ -191,6 +234,9 @@ def main(argv=None):
     elif args.study == "bubble":
         for p in precs:
             print(json.dumps(bubble(args.steps, args.every, p, case=args.case)), flush=True)
+    elif args.study == "rti":
+        for p in precs:
+            print(json.dumps(rti(args.edge, args.steps, args.every, p, "ABCD".index(args.model))), flush=True)
     else:
         for r in collision(args.edge, args.steps, args.every, tuple(precs)):
             print(json.dumps(r), flush=True)

@@ -48,3 +48,16 @@ def test_translating_droplet_64_against_oracle(prec):
     # the oracle's own Galilean-invariance error: the droplet lags u0 t by about 5 %
     last = run["samples"][-1]
     assert -12.0 < last["drift"][0] < -8.0 and abs(last["drift"][2]) < 1e-3
+
+
+def test_rayleigh_taylor_small_fp64_parity():
+    """The RTI setup of Sec. IV.E at W = 16 (walls, buoyancy, no tension), 200
+    steps: GPU FP64 against the oracle within 1e-12."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from parity_util import compare_macros, run_pair
+    from paper_2309_07801_gb300 import inputs
+    wl = inputs.rayleigh_taylor(16)
+    od, gd = run_pair(wl.params(), inputs.workload_fields(wl), 200, "f64")
+    m = compare_macros(od, gd)
+    assert max(m[k] for k in ("rho_r", "rho_b", "p", "phi", "u")) <= 1e-12, m

@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define CG27_ABI_VERSION 1
+#define CG27_ABI_VERSION 2
 
 /* return codes */
 #define CG_OK 0
@@ -52,9 +52,23 @@ extern "C" {
 #define CG_ERR_NONFINITE (-4)   /* a non-finite density was produced */
 #define CG_ERR_WORKSPACE (-5)   /* workspace missing, too small or misaligned */
 
-/* boundary kind per axis */
+/* boundary kind per axis.  Every wall kind makes cells 0 and n-1 of the axis
+ * solid and uses the fullway bounce-back scheme (Sec. IV, introduction: no-slip,
+ * slip and moving walls): what reaches a solid cell along c_j leaves it one step
+ * later along c_i, colour by colour.
+ *   BOUNCEBACK  c_i = -c_j (no-slip, wall at rest)
+ *   SLIP        c_i = c_j with the wall-normal component negated (specular)
+ *   MOVING      c_i = -c_j, plus 2 w_i rho_k (c_i . u_w) / c_s^2 for colour k,
+ *               rho_k of the fluid cell the population came from and u_w the
+ *               face's velocity in wall_u
+ * A solid cell on several wall faces (an edge or corner of the box) is a slip
+ * cell only if all those faces are slip walls (then every such normal component
+ * is negated); otherwise it bounces back, with the sum of the velocities of its
+ * moving faces.  Cells of the user's solid mask are no-slip walls at rest. */
 #define CG_BC_PERIODIC 0
-#define CG_BC_BOUNCEBACK 1 /* fullway bounce-back: cells 0 and n-1 are solid */
+#define CG_BC_BOUNCEBACK 1
+#define CG_BC_SLIP 2
+#define CG_BC_MOVING 3
 
 /* body force added to the interfacial force (Sec. IV test problems) */
 #define CG_FORCE_NONE 0
@@ -78,7 +92,7 @@ extern "C" {
 #define CG_BF16S 3 /* as CG_F16S with BF16 storage */
 
 typedef struct cg_params {
-  int32_t nx, ny, nz;     /* cells per axis, each >= 1 (>= 3 on a bounce-back axis) */
+  int32_t nx, ny, nz;     /* cells per axis, each >= 1 (>= 3 on a wall axis) */
   int32_t bc[3];          /* CG_BC_* per axis (x, y, z) */
   double rho_r0, rho_b0;  /* reference densities of the red and blue fluids (> 0) */
   double alpha_r, alpha_b;/* rest fractions in [0, 1); (c_s^k)^2 = (9/19)(1 - alpha_k) */
@@ -94,8 +108,11 @@ typedef struct cg_params {
   int32_t use_Q;          /* 1: apply the correction term Q (Sec. III.E); 0: omit it */
   int32_t precision;      /* CG_F64, CG_F32, CG_F16S or CG_BF16S */
   int32_t solid_mask;     /* 1: cg_init_fields() may be given a solid mask (reserves
-                             workspace for walls; implied by a bounce-back axis) */
+                             workspace for walls; implied by a wall axis) */
   int32_t reserved_;      /* must be 0 */
+  double wall_u[6][3];    /* velocity of the faces x-, x+, y-, y+, z-, z+ of a
+                             CG_BC_MOVING axis (finite; the component normal to
+                             the face must be 0); ignored for other kinds */
 } cg_params;
 
 typedef struct cg_ctx cg_ctx; /* opaque */
@@ -118,11 +135,12 @@ int cg_create(const cg_params *p, void *d_workspace, size_t bytes,
 
 /* Initialise from host fields: rho_r[N], rho_b[N] (> 0 where fluid), u[3N]
  * (the velocity of the equilibrium), solid[N] (nonzero = solid cell; may be
- * NULL; non-NULL needs params.solid_mask or a bounce-back axis).  Cells 0
- * and n-1 of a bounce-back axis are solid whatever the mask.  Every fluid
- * cell gets the post-collision populations f_i^k = (rho_k / rho)
- * f_i^eq(rho, p, u) of the selected model; solid cells start empty.  The
- * first cg_step() begins with streaming. */
+ * NULL; non-NULL needs params.solid_mask or a wall axis).  Cells 0 and n-1
+ * of a wall axis are solid whatever the mask.  Every fluid cell gets the
+ * post-collision populations f_i^k = (rho_k / rho) f_i^eq(rho, p, u) of the
+ * selected model; a solid cell starts with what the wall rule above makes of
+ * the populations its fluid neighbours send it in that state (so the first
+ * step sees no empty wall).  The first cg_step() begins with streaming. */
 int cg_init_fields(cg_ctx *ctx, const double *rho_r, const double *rho_b,
                    const double *u, const uint8_t *solid);
 

@@ -22,7 +22,7 @@ _SRC = os.path.join(_HERE, "cg_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 MODEL_A, MODEL_B, MODEL_C, MODEL_D = 0, 1, 2, 3
-BC_PERIODIC, BC_BOUNCEBACK = 0, 1
+BC_PERIODIC, BC_BOUNCEBACK, BC_SLIP, BC_MOVING = 0, 1, 2, 3
 FORCE_NONE, FORCE_CONST, FORCE_GRAVITY, FORCE_BUOYANCY = 0, 1, 2, 3
 FIELDS = {"grad_phi": (0, 3), "n": (1, 3), "kappa": (2, 1), "F": (3, 3),
           "Q": (4, 3), "omega1": (5, 1), "w": (6, 3), "R": (7, 3)}
@@ -52,7 +52,8 @@ class Params(ctypes.Structure):
                 ("omega", ctypes.c_double * 11), ("g", ctypes.c_double * 3),
                 ("rho_ref", ctypes.c_double),
                 ("force_mode", ctypes.c_int32), ("model", ctypes.c_int32),
-                ("use_Q", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("use_Q", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("wall_u", (ctypes.c_double * 3) * 6)]
 
 
 _lib = None
@@ -170,7 +171,7 @@ def threads() -> int:
 def make_params(nx, ny, nz, *, bc=(0, 0, 0), rho_r0=1.0, rho_b0=1.0,
                 alpha_r=8.0 / 27.0, alpha_b=8.0 / 27.0, nu_r=0.1, nu_b=0.1,
                 sigma=0.01, beta=0.7, omega=None, g=(0.0, 0.0, 0.0), rho_ref=0.0,
-                force_mode=FORCE_NONE, model=MODEL_D, use_Q=1) -> Params:
+                force_mode=FORCE_NONE, model=MODEL_D, use_Q=1, wall_u=None) -> Params:
     P = Params()
     P.nx, P.ny, P.nz = nx, ny, nz
     for a in range(3):
@@ -185,6 +186,10 @@ def make_params(nx, ny, nz, *, bc=(0, 0, 0), rho_r0=1.0, rho_b0=1.0,
         P.omega[q] = float(om[q])
     P.rho_ref = rho_ref
     P.force_mode, P.model, P.use_Q = force_mode, model, use_Q
+    if wall_u is not None:
+        for f in range(6):
+            for b in range(3):
+                P.wall_u[f][b] = float(wall_u[f][b])
     return P
 
 

@@ -534,6 +534,44 @@ static int64_t neighbour(const ocg_domain *d, int64_t cell, int i, int s) {
   return x + nx * (y + ny * z);
 }
 
+/* Which walls a solid cell belongs to.  Returns 1 when every wall face of the
+ * cell is a slip wall (then *flip has bit a set for each wall-normal axis a),
+ * 0 otherwise (no-slip: obstacles, no-slip or moving faces; *uw = the summed
+ * velocity of the moving faces). */
+static int wall_kind(const ocg_domain *d, int64_t cell, int *flip, double uw[3]) {
+  const int64_t n[3] = {d->p.nx, d->p.ny, d->p.nz};
+  const int64_t xyz[3] = {cell % n[0], (cell / n[0]) % n[1], cell / (n[0] * n[1])};
+  int faces = 0, slip = 0, other = 0;
+  *flip = 0;
+  uw[0] = uw[1] = uw[2] = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    if (d->p.bc[a] == OCG_BC_PERIODIC) continue;
+    int face = -1;
+    if (xyz[a] == 0) face = 2 * a;
+    else if (xyz[a] == n[a] - 1) face = 2 * a + 1;
+    if (face < 0) continue;
+    ++faces;
+    if (d->p.bc[a] == OCG_BC_SLIP) {
+      ++slip;
+      *flip |= 1 << a;
+    } else {
+      ++other;
+      if (d->p.bc[a] == OCG_BC_MOVING)
+        for (int b = 0; b < 3; ++b) uw[b] += d->p.wall_u[face][b];
+    }
+  }
+  return faces > 0 && other == 0 && slip > 0;
+}
+
+/* index of the velocity c_i with the components of the axes in `flip` negated */
+static int reflected(int i, int flip) {
+  int c[3];
+  for (int a = 0; a < 3; ++a) c[a] = (flip >> a) & 1 ? -CI[i][a] : CI[i][a];
+  for (int j = 0; j < 27; ++j)
+    if (CI[j][0] == c[0] && CI[j][1] == c[1] && CI[j][2] == c[2]) return j;
+  return i;
+}
+
 static double order_parameter(const ocg_domain *d, double rr, double rb) {
   double a = rr / d->p.rho_r0, b = rb / d->p.rho_b0;
   return (a + b > 0.0) ? (a - b) / (a + b) : 0.0;
@@ -545,9 +583,9 @@ int ocg_init(ocg_domain *d, const double *rho_r, const double *rho_b,
   for (int64_t c = 0; c < N; ++c) {
     int64_t x = c % d->p.nx, y = (c / d->p.nx) % d->p.ny, z = c / (d->p.nx * d->p.ny);
     uint8_t s = solid ? (solid[c] != 0) : 0;
-    if (d->p.bc[0] == OCG_BC_BOUNCEBACK && (x == 0 || x == d->p.nx - 1)) s = 1;
-    if (d->p.bc[1] == OCG_BC_BOUNCEBACK && (y == 0 || y == d->p.ny - 1)) s = 1;
-    if (d->p.bc[2] == OCG_BC_BOUNCEBACK && (z == 0 || z == d->p.nz - 1)) s = 1;
+    if (d->p.bc[0] != OCG_BC_PERIODIC && (x == 0 || x == d->p.nx - 1)) s = 1;
+    if (d->p.bc[1] != OCG_BC_PERIODIC && (y == 0 || y == d->p.ny - 1)) s = 1;
+    if (d->p.bc[2] != OCG_BC_PERIODIC && (z == 0 || z == d->p.nz - 1)) s = 1;
     d->solid[c] = s;
   }
 #ifdef _OPENMP
@@ -574,6 +612,34 @@ int ocg_init(ocg_domain *d, const double *rho_r, const double *rho_b,
     d->press[c] = p;
     d->phi[c] = order_parameter(d, rr, rb);
     for (int a = 0; a < 3; ++a) d->u[a * N + c] = uc[a];
+  }
+  /* walls start as if they had received the initial populations of their
+   * fluid neighbours one step earlier (the fullway rule of one_step applied
+   * to the initial state), so the first step sees no empty wall */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+  for (int64_t c = 0; c < N; ++c) {
+    if (!d->solid[c]) continue;
+    int flip;
+    double uw[3];
+    const int slip = wall_kind(d, c, &flip, uw);
+    for (int i = 0; i < 27; ++i) {
+      const int j = slip ? reflected(i, flip) : opposite(i);
+      const int64_t src = neighbour(d, c, j, -1);
+      double r = 0.0, b = 0.0;
+      if (!d->solid[src]) {
+        r = d->fr[j * N + src];
+        b = d->fb[j * N + src];
+        if (!slip) {
+          const double cu = CI[i][0] * uw[0] + CI[i][1] * uw[1] + CI[i][2] * uw[2];
+          r += 2.0 * weight(i) * rho_r[src] * cu / CS2;
+          b += 2.0 * weight(i) * rho_b[src] * cu / CS2;
+        }
+      }
+      d->fr[i * N + c] = r;
+      d->fb[i * N + c] = b;
+    }
   }
   return 0;
 }
@@ -708,10 +774,25 @@ static void one_step(ocg_domain *d) {
 #endif
   for (int64_t c = 0; c < N; ++c) {
     if (d->solid[c]) {
+      /* fullway bounce-back: what arrived along c_j leaves along c_i next step.
+       * No-slip and moving walls: j = opposite(i), and a moving wall adds
+       * 2 w_i rho_k (c_i . u_w) / c_s^2 to colour k of a population that came
+       * from a fluid cell, rho_k of that cell.  Slip walls: c_j is c_i with
+       * the wall-normal components negated (specular reflection). */
+      int flip;
+      double uw[3];
+      const int slip = wall_kind(d, c, &flip, uw);
       for (int i = 0; i < 27; ++i) {
-        int o = opposite(i);
-        d->fr[i * N + c] = d->gr[o * N + c];
-        d->fb[i * N + c] = d->gb[o * N + c];
+        const int j = slip ? reflected(i, flip) : opposite(i);
+        double r = d->gr[j * N + c], b = d->gb[j * N + c];
+        const int64_t src = neighbour(d, c, j, -1);
+        if (!slip && !d->solid[src]) {  /* momentum exchange with the fluid only */
+          const double cu = CI[i][0] * uw[0] + CI[i][1] * uw[1] + CI[i][2] * uw[2];
+          r += 2.0 * weight(i) * d->rho_r[src] * cu / CS2;
+          b += 2.0 * weight(i) * d->rho_b[src] * cu / CS2;
+        }
+        d->fr[i * N + c] = r;
+        d->fb[i * N + c] = b;
       }
       for (int a = 0; a < 3; ++a) d->R[a * N + c] = 0.0;
       d->om1[c] = 0.0;

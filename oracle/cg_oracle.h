@@ -29,13 +29,15 @@ extern "C" {
 #endif
 
 enum { OCG_MODEL_A = 0, OCG_MODEL_B = 1, OCG_MODEL_C = 2, OCG_MODEL_D = 3 };
-enum { OCG_BC_PERIODIC = 0, OCG_BC_BOUNCEBACK = 1 };
+/* walls (Sec. IV, introduction: no-slip, slip and moving walls, all by the
+ * fullway bounce-back scheme): the end layers of a non-periodic axis are solid */
+enum { OCG_BC_PERIODIC = 0, OCG_BC_BOUNCEBACK = 1, OCG_BC_SLIP = 2, OCG_BC_MOVING = 3 };
 enum { OCG_FORCE_NONE = 0, OCG_FORCE_CONST = 1, OCG_FORCE_GRAVITY = 2,
        OCG_FORCE_BUOYANCY = 3 };
 
 typedef struct ocg_params {
   int32_t nx, ny, nz;
-  int32_t bc[3];          /* per axis: periodic, or fullway bounce-back with
+  int32_t bc[3];          /* per axis: periodic, or a wall kind (OCG_BC_*) with
                              solid layers at index 0 and n-1 */
   double rho_r0, rho_b0;  /* reference densities (Sec. II.A, Eq. order parameter) */
   double alpha_r, alpha_b;/* rest fractions; (c_s^k)^2 = xi (1 - alpha_k) */
@@ -48,6 +50,7 @@ typedef struct ocg_params {
   int32_t model;          /* OCG_MODEL_* */
   int32_t use_Q;          /* 1: correction term Q of Sec. III.E applied */
   int32_t pad_;
+  double wall_u[6][3];    /* velocity of the walls x-, x+, y-, y+, z-, z+ (moving walls) */
 } ocg_params;
 
 /* lattice tables: c[27*3] (row i = c_ix,c_iy,c_iz), w[27] */

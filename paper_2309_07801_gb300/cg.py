@@ -17,7 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libcg27.so")
 
 CG_OK = 0
-CG_BC_PERIODIC, CG_BC_BOUNCEBACK = 0, 1
+CG_BC_PERIODIC, CG_BC_BOUNCEBACK, CG_BC_SLIP, CG_BC_MOVING = 0, 1, 2, 3
 CG_FORCE_NONE, CG_FORCE_CONST, CG_FORCE_GRAVITY, CG_FORCE_BUOYANCY = 0, 1, 2, 3
 CG_MODEL_A, CG_MODEL_B, CG_MODEL_C, CG_MODEL_D = 0, 1, 2, 3
 CG_F64, CG_F32, CG_F16S, CG_BF16S = 0, 1, 2, 3
@@ -41,7 +41,8 @@ class cg_params(ctypes.Structure):
                 ("rho_ref", ctypes.c_double),
                 ("force_mode", ctypes.c_int32), ("model", ctypes.c_int32),
                 ("use_Q", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("solid_mask", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
+                ("solid_mask", ctypes.c_int32), ("reserved_", ctypes.c_int32),
+                ("wall_u", (ctypes.c_double * 3) * 6)]
 
 
 # exported entry points of include/cg27.h: name -> (restype, argtypes)
@@ -231,6 +232,10 @@ def make_params(nx, ny, nz, *, precision="f32", **kw) -> cg_params:
             arr = getattr(p, key)
             for i, v in enumerate(val):
                 arr[i] = v
+        elif key == "wall_u":
+            for f, vec in enumerate(val):
+                for b, v in enumerate(vec):
+                    p.wall_u[f][b] = v
         else:
             setattr(p, key, val)
     return p

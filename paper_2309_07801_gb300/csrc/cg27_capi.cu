@@ -34,8 +34,8 @@ int settle(const cg_ctx* c) {
 }
 
 bool needs_solid(const cg_params& p) {
-  return p.solid_mask != 0 || p.bc[0] == CG_BC_BOUNCEBACK || p.bc[1] == CG_BC_BOUNCEBACK ||
-         p.bc[2] == CG_BC_BOUNCEBACK;
+  return p.solid_mask != 0 || p.bc[0] != CG_BC_PERIODIC || p.bc[1] != CG_BC_PERIODIC ||
+         p.bc[2] != CG_BC_PERIODIC;
 }
 
 int validate(const cg_params* p) {
@@ -46,10 +46,16 @@ int validate(const cg_params* p) {
   if (p->nz > 65535) return fail(CG_ERR_INVALID_ARG, "nz must be <= 65535");
   const int n[3] = {p->nx, p->ny, p->nz};
   for (int a = 0; a < 3; ++a) {
-    if (p->bc[a] != CG_BC_PERIODIC && p->bc[a] != CG_BC_BOUNCEBACK)
-      return fail(CG_ERR_INVALID_ARG, "bc must be CG_BC_PERIODIC or CG_BC_BOUNCEBACK");
-    if (p->bc[a] == CG_BC_BOUNCEBACK && n[a] < 3)
-      return fail(CG_ERR_INVALID_ARG, "a bounce-back axis needs at least 3 cells");
+    if (p->bc[a] < CG_BC_PERIODIC || p->bc[a] > CG_BC_MOVING)
+      return fail(CG_ERR_INVALID_ARG, "bc must be CG_BC_PERIODIC, BOUNCEBACK, SLIP or MOVING");
+    if (p->bc[a] != CG_BC_PERIODIC && n[a] < 3)
+      return fail(CG_ERR_INVALID_ARG, "a wall axis needs at least 3 cells");
+    for (int f = 2 * a; f < 2 * a + 2; ++f)
+      for (int b = 0; b < 3; ++b) {
+        if (!std::isfinite(p->wall_u[f][b])) return fail(CG_ERR_INVALID_ARG, "wall_u must be finite");
+        if (p->bc[a] == CG_BC_MOVING && b == a && p->wall_u[f][b] != 0.0)
+          return fail(CG_ERR_INVALID_ARG, "a moving wall moves in its own plane (normal component 0)");
+      }
   }
   if (!(p->rho_r0 > 0) || !(p->rho_b0 > 0)) return fail(CG_ERR_INVALID_ARG, "rho_r0, rho_b0 must be > 0");
   if (!(p->alpha_r >= 0 && p->alpha_r < 1) || !(p->alpha_b >= 0 && p->alpha_b < 1))
@@ -171,6 +177,13 @@ void enqueue_init(cg_ctx* c, const double* d_in) {
   Ptrs<T> P = make_ptrs<T>(c, 1);
   const long long n = c->L.n;
   k_init<T, SF, SOLID><<<gr, b, 0, c->stream>>>(g, P, make_phys<T>(c->prm), d_in, d_in + n, d_in + 2 * n, n);
+  if constexpr (SOLID) {
+    // walls from the fluid cells of the same buffer (read fluid, write solid)
+    Ptrs<T> W = make_ptrs<T>(c, 0);
+    W.f_out = const_cast<void*>(W.f_in);
+    W.aux_out = const_cast<T*>(W.aux_in);
+    k_init_walls<T, SF><<<gr, b, 0, c->stream>>>(g, W, make_phys<T>(c->prm), d_in, d_in + n);
+  }
 }
 
 }  // namespace
@@ -331,8 +344,8 @@ int cg_init_fields(cg_ctx* c, const double* rho_r, const double* rho_b, const do
     uint8_t* d_solid = reinterpret_cast<uint8_t*>(stage + align_up(5 * dbytes));
     if (solid)
       CG_CUDA(cudaMemcpyAsync(d_solid, solid, (size_t)n, cudaMemcpyHostToDevice, c->stream));
-    k_solid_self<<<gr, b, 0, c->stream>>>(g, d_solid, solid ? 1 : 0, c->prm.bc[0] == CG_BC_BOUNCEBACK,
-                                          c->prm.bc[1] == CG_BC_BOUNCEBACK, c->prm.bc[2] == CG_BC_BOUNCEBACK);
+    k_solid_self<<<gr, b, 0, c->stream>>>(g, d_solid, solid ? 1 : 0, c->prm.bc[0] != CG_BC_PERIODIC,
+                                          c->prm.bc[1] != CG_BC_PERIODIC, c->prm.bc[2] != CG_BC_PERIODIC);
     k_solid_mask<<<gr, b, 0, c->stream>>>(g, d_solid, reinterpret_cast<uint32_t*>(c->ws + c->L.mask));
   }
   switch (c->prm.precision) {

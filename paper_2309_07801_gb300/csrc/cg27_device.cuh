@@ -101,7 +101,12 @@ struct Phys {
   int force_mode, model, use_Q;
   int shift;  // populations stored as deviations from the rest state (16-bit modes)
   T rest1;    // p_ref / c_s^2: the moving rest-state populations are w_q rest1
+  int bc[3];         // wall kind per axis (the CG_BC_* values of cg27.h)
+  T wall_u[6][3];    // velocity of the faces x-, x+, y-, y+, z-, z+ (moving walls; else 0)
 };
+
+// wall kinds per axis, as in cg27.h
+constexpr int BC_PERIODIC = 0, BC_SLIP = 2, BC_MOVING = 3;
 
 // ---- population storage ---------------------------------------------------------------
 // FP64/FP32 store f_q itself.  The 16-bit modes store the deviation of f_q from
@@ -175,11 +180,15 @@ __device__ __forceinline__ SF* fout(void* p) { return static_cast<SF*>(p); }
 
 struct Cell {
   int idx;
+  int x, y, z;
   int xs[3], ys[3], zs[3];  // offsets of x-1, x, x+1 (etc.) with periodic wrap
 };
 
 // the cell (x, y, z), which must lie inside the domain
 __device__ __forceinline__ void make_cell_at(const Geom& g, int x, int y, int z, Cell& c) {
+  c.x = x;
+  c.y = y;
+  c.z = z;
   c.xs[0] = (x == 0 ? g.nx - 1 : x - 1);
   c.xs[1] = x;
   c.xs[2] = (x == g.nx - 1 ? 0 : x + 1);
@@ -238,6 +247,56 @@ __device__ __forceinline__ void pull_colour(const Ptrs<T>& P, long long stride, 
     fb = b * f - t;
     ft = f;
   }
+}
+
+// ---- walls (Sec. IV, introduction: no-slip, slip and moving walls, fullway) ---------------
+// Rule of a solid cell: returns the axes whose velocity component a slip wall
+// negates (nonzero: specular reflection) or 0 for bounce-back, with uw the
+// summed velocity of the cell's moving faces.  A cell is a slip cell only if
+// all of its wall faces are slip walls; obstacle cells bounce back at rest.
+template <typename T>
+__device__ __forceinline__ int wall_rule(const Geom& g, const Phys<T>& ph, const Cell& c, T (&uw)[3]) {
+  const int xyz[3] = {c.x, c.y, c.z}, n[3] = {g.nx, g.ny, g.nz};
+  int slip = 0, other = 0, flip = 0;
+  uw[0] = uw[1] = uw[2] = T(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (ph.bc[a] == BC_PERIODIC) continue;
+    const int face = xyz[a] == 0 ? 2 * a : (xyz[a] == n[a] - 1 ? 2 * a + 1 : -1);
+    if (face < 0) continue;
+    if (ph.bc[a] == BC_SLIP) {
+      ++slip;
+      flip |= 1 << a;
+    } else {
+      ++other;
+      if (ph.bc[a] == BC_MOVING)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) uw[b] += ph.wall_u[face][b];
+    }
+  }
+  return (other == 0 && slip > 0) ? flip : 0;
+}
+
+// direction q with the components of the axes in `flip` negated
+__device__ __forceinline__ int reflect_dir(int q, int flip) {
+  const int cx = (flip & 1) ? -CX(q) : CX(q);
+  const int cy = (flip & 2) ? -CY(q) : CY(q);
+  const int cz = (flip & 4) ? -CZ(q) : CZ(q);
+  return (cx + 1) + 3 * (cy + 1) + 9 * (cz + 1);
+}
+
+// The wall rule applied to the colour parts (fr, fb) of the population that
+// arrived along c_q from the cell src: returns the direction it leaves along
+// next step and adds the moving-wall term 2 w_i rho_k (c_i . u_w) / c_s^2
+// (rho_k of the source cell: rr, rb) for a bounce-back cell.
+template <typename T>
+__device__ __forceinline__ int wall_emit(int q, int flip, const T (&uw)[3], T rr, T rb, T& fr, T& fb) {
+  if (flip) return reflect_dir(q, flip);
+  const T cu = T(CX(q)) * uw[0] + T(CY(q)) * uw[1] + T(CZ(q)) * uw[2];  // c_q . u_w = -c_i . u_w
+  const T k = -T(2) * WQ<T>(q) * cu / Lat<T>::CS2;
+  fr += k * rr;
+  fb += k * rb;
+  return OPP(q);
 }
 
 // ---- order parameter, Eq. (order parameter) --------------------------------------
@@ -524,6 +583,35 @@ __global__ void __launch_bounds__(128) k_init(Geom g, Ptrs<T> P, Phys<T> ph, con
 }
 
 // macroscopic fields to FP64: [rho_r][rho_b][u 3][p][phi], each n long
+// Initial content of the wall cells: the wall rule applied to the initial
+// populations of their fluid neighbours (buffer read for fluid cells and
+// written for solid cells only), with the initial colour densities rr_in, rb_in.
+template <typename T, typename SF>
+__global__ void __launch_bounds__(128) k_init_walls(Geom g, Ptrs<T> P, Phys<T> ph, const double* rr_in,
+                                                    const double* rb_in) {
+  Cell c;
+  if (!make_cell(g, c)) return;
+  const long long S = g.stride;
+  const int i0 = c.idx;
+  const uint32_t mask = ld(P.mask + i0);
+  if (!((mask >> SELF_SOLID_BIT) & 1u)) return;
+  T uw[3];
+  const int flip = wall_rule(g, ph, c, uw);
+  for (int q = 0; q < 27; ++q) {
+    const int src = nbr(c, -CX(q), -CY(q), -CZ(q));
+    T fr = T(0), fb = T(0), ft;
+    int out;
+    if (!((mask >> OPP(q)) & 1u)) {  // the source is fluid
+      pull_colour<T, SF, true>(P, S, q, src, mask, fr, fb, ft);
+      out = wall_emit(q, flip, uw, T(rr_in[src]), T(rb_in[src]), fr, fb);
+    } else {
+      out = flip ? reflect_dir(q, flip) : OPP(q);
+    }
+    fout<SF>(P.f_out)[out * S + i0] = Store<SF>::put(fr);
+    P.aux_out[out * S + i0] = fb;
+  }
+}
+
 template <typename T, bool SOLID>
 __global__ void __launch_bounds__(128) k_read_macros(Geom g, Ptrs<T> P, Phys<T> ph, double* out,
                                                      long long n) {

@@ -87,6 +87,9 @@ inline Phys<T> make_phys(const cg_params& p) {
   ph.shift = (p.precision == CG_F16S || p.precision == CG_BF16S) ? 1 : 0;
   // reference pressure of the red phase at its reference density
   ph.rest1 = T(3.0 * p.rho_r0 * xi * (1.0 - p.alpha_r));
+  for (int a = 0; a < 3; ++a) ph.bc[a] = p.bc[a];
+  for (int f = 0; f < 6; ++f)
+    for (int b = 0; b < 3; ++b) ph.wall_u[f][b] = T(p.bc[f / 2] == CG_BC_MOVING ? p.wall_u[f][b] : 0.0);
   return ph;
 }
 

@@ -634,14 +634,19 @@ __device__ __forceinline__ void collide_cell(const Geom& g, const Ptrs<T>& P, co
   const int i0 = c.idx;
   const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
   if (SOLID && ((mask >> SELF_SOLID_BIT) & 1u)) {
-    // fullway bounce-back: keep what streamed in, reversed, colour by colour
-#pragma unroll
+    // fullway walls: keep what streamed in, colour by colour, and send it back
+    // by the cell's wall rule (bounce-back, specular, or moving)
+    T uw[3];
+    const int flip = wall_rule(g, ph, c, uw);
     for (int q = 0; q < 27; ++q) {
       const int src = nbr(c, -CX(q), -CY(q), -CZ(q));
       T fr, fb, ft;
       pull_colour<T, SF, SOLID>(P, S, q, src, mask, fr, fb, ft);
-      fout<SF>(P.f_out)[OPP(q) * S + i0] = Store<SF>::put(fr);
-      P.aux_out[OPP(q) * S + i0] = fb;
+      const bool fluid_src = !((mask >> OPP(q)) & 1u);
+      const int out = wall_emit(q, flip, uw, fluid_src ? ld(P.mac + src) : T(0),
+                                fluid_src ? ld(P.mac + S + src) : T(0), fr, fb);
+      fout<SF>(P.f_out)[out * S + i0] = Store<SF>::put(fr);
+      P.aux_out[out * S + i0] = fb;
     }
     return;
   }

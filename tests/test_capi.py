@@ -36,8 +36,8 @@ def test_every_declared_symbol_is_exported(cg):
 def test_params_struct_layout_matches_header(cg):
     # offsets follow the C declaration order; size includes the trailing ints
     p = cg.cg_params()
-    assert ctypes.sizeof(p) == 4 * 6 + 8 * 8 + 8 * 11 + 8 * 3 + 8 + 4 * 6
-    assert cg.cg_abi_version() == 1
+    assert ctypes.sizeof(p) == 4 * 6 + 8 * 8 + 8 * 11 + 8 * 3 + 8 + 4 * 6 + 8 * 18
+    assert cg.cg_abi_version() == 2
 
 
 def test_defaults_and_workspace(cg):
@@ -116,3 +116,20 @@ def test_16_bit_storage_size_limit(cg):
     assert e.value.code == -2
     p.precision = cg.CG_F32
     assert cg.cg_workspace_bytes(p) > 0
+
+
+def test_wall_kinds_validated(cg):
+    wall_u = [[0.0] * 3 for _ in range(6)]
+    wall_u[5] = [0.02, 0.0, 0.0]
+    p = cg.make_params(8, 8, 8, bc=(cg.CG_BC_SLIP, 0, cg.CG_BC_MOVING), wall_u=wall_u)
+    assert cg.cg_workspace_bytes(p) > cg.cg_workspace_bytes(cg.make_params(8, 8, 8))  # walls reserve AUX
+    wall_u[5] = [0.0, 0.0, 0.01]  # a moving wall must move in its own plane
+    with pytest.raises(cg.CGError):
+        cg.cg_workspace_bytes(cg.make_params(8, 8, 8, bc=(0, 0, cg.CG_BC_MOVING), wall_u=wall_u))
+    wall_u[5] = [float("nan"), 0.0, 0.0]
+    with pytest.raises(cg.CGError):
+        cg.cg_workspace_bytes(cg.make_params(8, 8, 8, bc=(0, 0, cg.CG_BC_MOVING), wall_u=wall_u))
+    with pytest.raises(cg.CGError):
+        cg.cg_workspace_bytes(cg.make_params(8, 8, 2, bc=(0, 0, cg.CG_BC_SLIP)))
+    with pytest.raises(cg.CGError):
+        cg.cg_workspace_bytes(cg.make_params(8, 8, 8, bc=(0, 4, 0)))

@@ -98,6 +98,46 @@ def test_f64_bounceback_walls(bc):
     assert np.all(np.abs(gd.mass()[0] - od.mass()) / od.mass() < 1e-13)
 
 
+def _walls(**faces):
+    """wall_u from face names (xm, xp, ym, yp, zm, zp) to velocity vectors."""
+    order = ("xm", "xp", "ym", "yp", "zm", "zp")
+    return [list(faces.get(f, (0.0, 0.0, 0.0))) for f in order]
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 2), (2, 0, 2), (2, 2, 2)])
+def test_f64_slip_walls(bc):
+    """Specular walls, with slip-slip edges and corners."""
+    params = _ratio_params(10, 9, 12, bc=bc, force_mode=2, g=(1e-5, 0.0, -2e-5))
+    od, gd = run_pair(params, _droplet(params, seed=13), 60, "f64")
+    _assert_f64(od, gd)
+    assert np.all(np.abs(gd.mass()[0] - od.mass()) / od.mass() < 1e-13)
+
+
+def test_f64_moving_walls_tube():
+    """The moving tube of Sec. IV.B in 3D: ratio 3 droplet between z walls that
+    both move at U along x."""
+    U = 0.02
+    params = _ratio_params(12, 8, 14, ratio=3.0, bc=(0, 0, 3), wall_u=_walls(zm=(U, 0, 0), zp=(U, 0, 0)))
+    od, gd = run_pair(params, _droplet(params, seed=17, u0=(0.0, 0.0, 0.0)), 80, "f64")
+    _assert_f64(od, gd)
+
+
+def test_f64_mixed_wall_kinds_and_corners():
+    """No-slip x walls, moving y walls (opposite directions along z), slip z
+    walls: every kind of edge and corner rule."""
+    params = _ratio_params(9, 10, 11, bc=(1, 3, 2), force_mode=1, g=(0.0, 0.0, 1e-5),
+                           wall_u=_walls(ym=(0.0, 0.0, 0.01), yp=(-0.015, 0.0, 0.02)))
+    od, gd = run_pair(params, _droplet(params, seed=19), 50, "f64")
+    _assert_f64(od, gd)
+
+
+def test_f32_moving_and_slip_walls():
+    params = _ratio_params(16, 12, 18, ratio=3.0, bc=(2, 0, 3), wall_u=_walls(zm=(0.02, 0, 0), zp=(-0.02, 0, 0)))
+    od, gd = run_pair(params, _droplet(params, seed=23), 200, "f32")
+    m = compare_macros(od, gd)
+    assert m["rho_cellrel"] <= 1e-5 and m["u_abs"] <= 1e-6, m
+
+
 def test_f64_solid_mask_obstacle_general_rates():
     params = _ratio_params(14, 10, 9, bc=(0, 0, 1), omega=[1.2] * 11, force_mode=1,
                            g=(3e-5, 0.0, 0.0))

@@ -182,3 +182,71 @@ def test_laplace_law_cylinder(orc):
     Reff = math.sqrt(((1 + m["phi"][0]) / 2).sum() / math.pi)
     sig = Reff * (p[r < R - 4].mean() - p[r > R + 4].mean())
     assert abs(sig - sigma) / sigma < 0.03, sig
+
+
+# ---- wall kinds (Sec. IV, introduction: no-slip, slip, moving, fullway) --------
+
+def _mixture(nx, ny, nz):
+    """Uniform 50/50 mixture: phi = 0 everywhere, so there is no interface."""
+    return (np.full((nz, ny, nx), 0.5), np.full((nz, ny, nx), 0.5), np.zeros((3, nz, ny, nx)))
+
+
+def test_slip_walls_keep_a_uniform_wall_parallel_flow(orc):
+    """Specular reflection maps the equilibrium of a flow parallel to the wall
+    onto itself, so a uniform flow between slip walls is a fixed point (the
+    no-slip walls of the same channel slow it down)."""
+    nx, ny, nz, U, steps = 3, 2, 10, 0.03, 50
+    rr, rb, u = _mixture(nx, ny, nz)
+    u[0] = U
+    u[1] = -0.5 * U
+    P = orc.make_params(nx, ny, nz, bc=(0, 0, orc.BC_SLIP), sigma=0.0)
+    d = orc.Domain(P)
+    d.init(rr, rb, u)
+    d.step(steps)
+    m = d.macros()["u"][:, 1:-1]
+    assert np.abs(m[0] - U).max() < 1e-15 and np.abs(m[1] + 0.5 * U).max() < 1e-15
+    assert np.abs(m[2]).max() < 1e-15
+    P.bc[2] = orc.BC_BOUNCEBACK
+    d2 = orc.Domain(P)
+    d2.init(rr, rb, u)
+    d2.step(steps)
+    u2 = d2.macros()["u"][0, 1:-1, 0, 0]
+    assert u2[0] < 0.9 * U and u2[len(u2) // 2] < U
+
+
+def test_moving_wall_couette_profile(orc):
+    """Bottom wall at rest, top wall at U: the steady profile is linear between
+    the wall positions, halfway between the solid and the first fluid layer."""
+    nx, ny, nz, U = 2, 2, 14, 0.02
+    wall_u = [[0.0] * 3 for _ in range(6)]
+    wall_u[5] = [U, 0.0, 0.0]
+    P = orc.make_params(nx, ny, nz, bc=(0, 0, orc.BC_MOVING), sigma=0.0, nu_r=0.2, nu_b=0.2,
+                        wall_u=wall_u)
+    d = orc.Domain(P)
+    d.init(*_mixture(nx, ny, nz))
+    mass0 = d.mass()
+    d.step(3000)
+    m = d.macros()
+    z = np.arange(1, nz - 1)
+    exact = U * (z - 0.5) / (nz - 2)
+    ux = m["u"][0, 1:-1, 0, 0]
+    # converged (3000 steps, 40 diffusion times); the fullway walls sit halfway
+    # between the layers to 1e-6 of U here
+    assert np.abs(ux - exact).max() < 1e-5 * U, np.abs(ux - exact).max()
+    assert np.abs(m["u"][2, 1:-1]).max() < 1e-12
+    assert np.allclose(d.mass(), mass0, rtol=1e-13)
+
+
+def test_slip_walls_conserve_colour_mass_with_a_droplet(orc):
+    """A droplet pushed against slip walls on two axes (corner cells too)."""
+    from paper_2309_07801_gb300 import inputs
+    n = 14
+    rr, rb, u = inputs.droplet_fields((n, n, n), (6.0, 7.0, 5.0), 3.5, 1.0, 0.5)
+    P = orc.make_params(n, n, n, bc=(orc.BC_SLIP, 0, orc.BC_SLIP), rho_r0=1.0, rho_b0=0.5,
+                        alpha_r=1.0 - (19.0 / 27.0) / 2.0, g=(-1e-4, 0.0, -1e-4),
+                        force_mode=orc.FORCE_CONST)
+    d = orc.Domain(P)
+    d.init(rr, rb, u)
+    m0 = d.mass()
+    d.step(60)
+    assert np.allclose(d.mass(), m0, rtol=1e-13, atol=0)

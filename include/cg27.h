@@ -30,7 +30,8 @@
  *     the last error of the calling thread is returned by cg_last_error().
  *     No exception crosses the ABI.
  *   - Population order at the ABI (cg_read_populations) is the 27-velocity
- *     order printed in Sec. II.A; the opposite of odd i is i + 1.
+ *     order printed in Sec. II.A (the opposite of odd i is i + 1), or for a
+ *     D2Q9 domain the 9-velocity order printed in App. A ([9][N] arrays).
  */
 #ifndef CG27_H
 #define CG27_H
@@ -82,6 +83,10 @@ extern "C" {
 #define CG_MODEL_C 2 /* g^{eq,6}, Phi_i up to O(u^3) (Li et al.) (Sec. III.C) */
 #define CG_MODEL_D 3 /* generalized equilibria, Phi_i up to O(u^6) (Sec. III.D) */
 
+/* lattice */
+#define CG_D3Q27 0
+#define CG_D2Q9 1 /* the two-dimensional variant of App. A */
+
 /* storage and arithmetic precision */
 #define CG_F64 0   /* FP64 storage and arithmetic */
 #define CG_F32 1   /* FP32 storage and arithmetic */
@@ -109,7 +114,9 @@ typedef struct cg_params {
   int32_t precision;      /* CG_F64, CG_F32, CG_F16S or CG_BF16S */
   int32_t solid_mask;     /* 1: cg_init_fields() may be given a solid mask (reserves
                              workspace for walls; implied by a wall axis) */
-  int32_t reserved_;      /* must be 0 */
+  int32_t lattice;        /* CG_D3Q27 (default) or CG_D2Q9 (App. A: nz = 1,
+                             bc[2] periodic, periodic or bounce-back x/y, no
+                             solid mask, Model D, FP64 or FP32) */
   double wall_u[6][3];    /* velocity of the faces x-, x+, y-, y+, z-, z+ of a
                              CG_BC_MOVING axis (finite; the component normal to
                              the face must be 0); ignored for other kinds */

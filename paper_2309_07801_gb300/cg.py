@@ -21,6 +21,7 @@ CG_BC_PERIODIC, CG_BC_BOUNCEBACK, CG_BC_SLIP, CG_BC_MOVING = 0, 1, 2, 3
 CG_FORCE_NONE, CG_FORCE_CONST, CG_FORCE_GRAVITY, CG_FORCE_BUOYANCY = 0, 1, 2, 3
 CG_MODEL_A, CG_MODEL_B, CG_MODEL_C, CG_MODEL_D = 0, 1, 2, 3
 CG_F64, CG_F32, CG_F16S, CG_BF16S = 0, 1, 2, 3
+CG_D3Q27, CG_D2Q9 = 0, 1
 PRECISIONS = {"f64": CG_F64, "f32": CG_F32, "f16s": CG_F16S, "bf16s": CG_BF16S}
 
 
@@ -41,7 +42,7 @@ class cg_params(ctypes.Structure):
                 ("rho_ref", ctypes.c_double),
                 ("force_mode", ctypes.c_int32), ("model", ctypes.c_int32),
                 ("use_Q", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("solid_mask", ctypes.c_int32), ("reserved_", ctypes.c_int32),
+                ("solid_mask", ctypes.c_int32), ("lattice", ctypes.c_int32),
                 ("wall_u", (ctypes.c_double * 3) * 6)]
 
 
@@ -254,6 +255,7 @@ class Domain:
         self.h = cg_create(params, self.workspace.data_ptr(), self.nbytes, self.stream.cuda_stream)
         self.shape = (params.nz, params.ny, params.nx)
         self.N = params.nx * params.ny * params.nz
+        self.nq = 9 if params.lattice == CG_D2Q9 else 27
 
     def close(self):
         if getattr(self, "h", None):
@@ -285,10 +287,10 @@ class Domain:
                 "p": p.reshape(sh), "phi": phi.reshape(sh)}
 
     def populations(self):
-        fr = np.empty(27 * self.N)
-        fb = np.empty(27 * self.N)
+        fr = np.empty(self.nq * self.N)
+        fb = np.empty(self.nq * self.N)
         cg_read_populations(self.h, fr, fb)
-        return fr.reshape((27,) + self.shape), fb.reshape((27,) + self.shape)
+        return fr.reshape((self.nq,) + self.shape), fb.reshape((self.nq,) + self.shape)
 
     def mass(self):
         return cg_reduce(self.h)

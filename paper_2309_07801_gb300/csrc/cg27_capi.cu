@@ -2,6 +2,7 @@
 // workspace layout, kernel launches of one time step, initialisation,
 // read-back, reductions and checkpoints.  Device code is in cg27_device.cuh.
 #include "cg27_host.cuh"
+#include "cg27_d2q9.cuh"
 
 #include <cmath>
 #include <cstdio>
@@ -21,6 +22,12 @@ int paper_to_lex(int i) {
       {0, -1, 1},  {1, 0, 1},  {-1, 0, -1}, {1, 0, -1},  {-1, 0, 1},  {1, 1, 1},   {-1, -1, -1},
       {1, 1, -1},  {-1, -1, 1}, {1, -1, 1}, {-1, 1, -1}, {-1, 1, 1},  {1, -1, -1}};
   return (C[i][0] + 1) + 3 * (C[i][1] + 1) + 9 * (C[i][2] + 1);
+}
+
+// D2Q9 velocity order of App. A -> lexicographic storage index (c_x + 1) + 3 (c_y + 1)
+int paper_to_lex2(int i) {
+  static const int C[9][2] = {{0, 0}, {1, 0}, {-1, 0}, {0, 1}, {0, -1}, {1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
+  return (C[i][0] + 1) + 3 * (C[i][1] + 1);
 }
 
 constexpr int RED_THREADS = 256;
@@ -75,7 +82,16 @@ int validate(const cg_params* p) {
   if ((p->precision == CG_F16S || p->precision == CG_BF16S) &&
       27.0 * (((double)p->nx * p->ny * p->nz + 63) / 64 * 64) >= 4294967296.0)
     return fail(CG_ERR_UNSUPPORTED, "16-bit population storage is limited to 159 million cells");
-  if (p->reserved_ != 0) return fail(CG_ERR_INVALID_ARG, "reserved_ must be 0");
+  if (p->lattice != CG_D3Q27 && p->lattice != CG_D2Q9) return fail(CG_ERR_INVALID_ARG, "unknown lattice");
+  if (p->lattice == CG_D2Q9) {
+    if (p->nz != 1) return fail(CG_ERR_INVALID_ARG, "a D2Q9 domain has nz = 1");
+    if (p->bc[2] != CG_BC_PERIODIC) return fail(CG_ERR_INVALID_ARG, "a D2Q9 domain has bc[2] = CG_BC_PERIODIC");
+    if (p->bc[0] > CG_BC_BOUNCEBACK || p->bc[1] > CG_BC_BOUNCEBACK)
+      return fail(CG_ERR_UNSUPPORTED, "D2Q9 supports periodic and bounce-back axes");
+    if (p->solid_mask) return fail(CG_ERR_UNSUPPORTED, "D2Q9 takes no solid mask");
+    if (p->model != CG_MODEL_D) return fail(CG_ERR_UNSUPPORTED, "D2Q9 implements the generalized equilibria (Model D) of App. A");
+    if (p->precision != CG_F64 && p->precision != CG_F32) return fail(CG_ERR_UNSUPPORTED, "D2Q9 runs in FP64 or FP32");
+  }
   return CG_OK;
 }
 
@@ -87,6 +103,7 @@ Layout make_layout(const cg_params& p) {
   L.pop_elem = (p.precision == CG_F64) ? 8 : (p.precision == CG_F32 ? 4 : 2);
   L.ns = (p.precision == CG_F16S || p.precision == CG_BF16S) ? 7 : 6;
   L.solid = needs_solid(p);
+  L.nq = p.lattice == CG_D2Q9 ? 9 : 27;
   L.red_blocks = (int)std::min<long long>(1024, (L.n + RED_THREADS - 1) / RED_THREADS);
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -95,10 +112,10 @@ Layout make_layout(const cg_params& p) {
     return at;
   };
   const size_t field = (size_t)L.stride * L.elem;
-  for (int b = 0; b < 2; ++b) L.f[b] = take(27 * (size_t)L.stride * L.pop_elem);
+  for (int b = 0; b < 2; ++b) L.f[b] = take(L.nq * (size_t)L.stride * L.pop_elem);
   for (int b = 0; b < 2; ++b) L.s[b] = take(L.ns * field);
   if (L.solid) {
-    for (int b = 0; b < 2; ++b) L.aux[b] = take(27 * field);
+    for (int b = 0; b < 2; ++b) L.aux[b] = take(L.nq * field);
     L.mask = take((size_t)L.stride * 4);
   }
   L.mac = take(5 * field);
@@ -153,7 +170,38 @@ void enqueue_step(cg_ctx* c) {
   if (ev) cudaEventRecord(ev[4], c->stream);
 }
 
+// one D2Q9 step: five per-cell kernels (the normal and force kernels are
+// timed together as the field pass)
+template <typename T, bool SOLID>
+void enqueue_step2(cg_ctx* c) {
+  const int cur = (int)(c->steps & 1);
+  const Geom g = make_geom(c);
+  const dim3 b = block_of(c->prm), gr = grid_of(c->prm, b);
+  const Ptrs<T> P = make_ptrs<T>(c, cur);
+  const Phys<T> ph = make_phys<T>(c->prm);
+  cudaEvent_t* ev = nullptr;
+  if (c->prof_used < c->prof_capacity) ev = &c->events[NUM_EVENTS_PER_STEP * c->prof_used++];
+  if (ev) cudaEventRecord(ev[0], c->stream);
+  k2_macro<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph);
+  if (ev) cudaEventRecord(ev[1], c->stream);
+  k2_normal<T, SOLID><<<gr, b, 0, c->stream>>>(g, P);
+  k2_force<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph);
+  if (ev) cudaEventRecord(ev[2], c->stream);
+  k2_qcorr<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, c->prm.use_Q);
+  if (ev) cudaEventRecord(ev[3], c->stream);
+  k2_collide<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph);
+  if (ev) cudaEventRecord(ev[4], c->stream);
+}
+
 void enqueue_step_any(cg_ctx* c) {
+  if (c->prm.lattice == CG_D2Q9) {
+    if (c->prm.precision == CG_F64) {
+      if (c->L.solid) enqueue_step2<double, true>(c); else enqueue_step2<double, false>(c);
+    } else {
+      if (c->L.solid) enqueue_step2<float, true>(c); else enqueue_step2<float, false>(c);
+    }
+    return;
+  }
   switch (c->prm.precision) {
     case CG_F64:
       if (c->L.solid) enqueue_step<double, double, true>(c); else enqueue_step<double, double, false>(c);
@@ -168,6 +216,21 @@ void enqueue_step_any(cg_ctx* c) {
 
 // the population buffer not holding the current state: free between steps
 char* scratch_of(const cg_ctx* c) { return c->ws + c->L.f[1 - (int)(c->steps & 1)]; }
+
+template <typename T, bool SOLID>
+void enqueue_init2(cg_ctx* c, const double* d_in) {
+  const Geom g = make_geom(c);
+  const dim3 b = block_of(c->prm), gr = grid_of(c->prm, b);
+  Ptrs<T> P = make_ptrs<T>(c, 1);  // the initial state goes to buffer 0
+  const long long n = c->L.n;
+  k2_init<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, make_phys<T>(c->prm), d_in, d_in + n, d_in + 2 * n, n);
+  if constexpr (SOLID) {
+    Ptrs<T> W = make_ptrs<T>(c, 0);
+    W.f_out = const_cast<void*>(W.f_in);
+    W.aux_out = const_cast<T*>(W.aux_in);
+    k2_init_walls<T><<<gr, b, 0, c->stream>>>(g, W);
+  }
+}
 
 template <typename T, typename SF, bool SOLID>
 void enqueue_init(cg_ctx* c, const double* d_in) {
@@ -202,6 +265,15 @@ __global__ void k_solid_self(Geom g, uint8_t* solid, int has_user, int bx, int b
   if (by && (y == 0 || y == g.ny - 1)) s = 1;
   if (bz && (z == 0 || z == g.nz - 1)) s = 1;
   solid[i] = s;
+}
+
+__global__ void k2_solid_mask(Geom g, const uint8_t* solid, uint32_t* mask) {
+  Cell2 c;
+  if (!make_cell2(g, c)) return;
+  uint32_t m = solid[c.idx] ? (1u << SELF_SOLID_BIT) : 0u;
+  for (int q = 0; q < 9; ++q)
+    if (solid[nbr2(c, CX2(q), CY2(q))]) m |= (1u << q);
+  mask[c.idx] = m;
 }
 
 __global__ void k_solid_mask(Geom g, const uint8_t* solid, uint32_t* mask) {
@@ -346,8 +418,18 @@ int cg_init_fields(cg_ctx* c, const double* rho_r, const double* rho_b, const do
       CG_CUDA(cudaMemcpyAsync(d_solid, solid, (size_t)n, cudaMemcpyHostToDevice, c->stream));
     k_solid_self<<<gr, b, 0, c->stream>>>(g, d_solid, solid ? 1 : 0, c->prm.bc[0] != CG_BC_PERIODIC,
                                           c->prm.bc[1] != CG_BC_PERIODIC, c->prm.bc[2] != CG_BC_PERIODIC);
-    k_solid_mask<<<gr, b, 0, c->stream>>>(g, d_solid, reinterpret_cast<uint32_t*>(c->ws + c->L.mask));
+    if (c->prm.lattice == CG_D2Q9)
+      k2_solid_mask<<<gr, b, 0, c->stream>>>(g, d_solid, reinterpret_cast<uint32_t*>(c->ws + c->L.mask));
+    else
+      k_solid_mask<<<gr, b, 0, c->stream>>>(g, d_solid, reinterpret_cast<uint32_t*>(c->ws + c->L.mask));
   }
+  if (c->prm.lattice == CG_D2Q9) {
+    if (c->prm.precision == CG_F64) {
+      if (c->L.solid) enqueue_init2<double, true>(c, d_in); else enqueue_init2<double, false>(c, d_in);
+    } else {
+      if (c->L.solid) enqueue_init2<float, true>(c, d_in); else enqueue_init2<float, false>(c, d_in);
+    }
+  } else
   switch (c->prm.precision) {
     case CG_F64:
       if (c->L.solid) enqueue_init<double, double, true>(c, d_in); else enqueue_init<double, double, false>(c, d_in);
@@ -419,13 +501,25 @@ int cg_read_populations(cg_ctx* c, double* fr, double* fb) {
   // the current state sits in buffer `cur`: read it through the "input" pointers
   const int cur = (int)(c->steps & 1);
   const size_t db = (size_t)n * sizeof(double);
-  for (int i = 0; i < 27; ++i) {
-    const int q = paper_to_lex(i);
-    if (c->prm.precision == CG_F64) {
+  for (int i = 0; i < c->L.nq; ++i) {
+    if (c->prm.lattice == CG_D2Q9) {
+      const int q = paper_to_lex2(i);
+      if (c->prm.precision == CG_F64) {
+        auto P = make_ptrs<double>(c, cur);
+        if (c->L.solid) k2_read_pop<double, true><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + n);
+        else k2_read_pop<double, false><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + n);
+      } else {
+        auto P = make_ptrs<float>(c, cur);
+        if (c->L.solid) k2_read_pop<float, true><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + n);
+        else k2_read_pop<float, false><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + n);
+      }
+    } else if (c->prm.precision == CG_F64) {
+      const int q = paper_to_lex(i);
       auto P = make_ptrs<double>(c, cur);
       if (c->L.solid) k_read_pop<double, double, true><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), q, d_out, d_out + n);
       else k_read_pop<double, double, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), q, d_out, d_out + n);
     } else {
+      const int q = paper_to_lex(i);
       auto P = make_ptrs<float>(c, cur);
       if (c->prm.precision == CG_F16S)
         k_read_pop<float, __half, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + n);
@@ -525,12 +619,12 @@ int state_regions(const cg_ctx* c, size_t off[6], size_t len[6]) {
   const int cur = (int)(c->steps & 1);
   const size_t field = (size_t)L.stride * L.elem;
   int k = 0;
-  off[k] = L.f[cur]; len[k++] = 27 * (size_t)L.stride * L.pop_elem;
+  off[k] = L.f[cur]; len[k++] = L.nq * (size_t)L.stride * L.pop_elem;
   off[k] = L.s[cur]; len[k++] = L.ns * field;
   off[k] = L.mac; len[k++] = 5 * field;
   off[k] = L.force; len[k++] = 3 * field;
   if (L.solid) {
-    off[k] = L.aux[cur]; len[k++] = 27 * field;
+    off[k] = L.aux[cur]; len[k++] = L.nq * field;
     off[k] = L.mask; len[k++] = (size_t)L.stride * 4;
   }
   return k;

@@ -34,6 +34,7 @@ struct Layout {
   size_t elem = 0;      // bytes of an arithmetic value (FP64 or FP32)
   size_t pop_elem = 0;  // bytes of a stored population
   int ns = 6;           // fields of the recoloring state
+  int nq = 27;          // populations per cell (27 for D3Q27, 9 for D2Q9)
   bool solid = false;
   int red_blocks = 0;
   size_t f[2] = {0, 0}, s[2] = {0, 0}, aux[2] = {0, 0};
@@ -67,7 +68,9 @@ namespace cg27 {
 template <typename T>
 inline Phys<T> make_phys(const cg_params& p) {
   Phys<T> ph;
-  const double xi = 9.0 / 19.0;
+  // EOS constant: (c_s^k)^2 = xi (1 - alpha_k); xi = 9/19 for D3Q27 (Sec. II.A),
+  // 3/5 for D2Q9 (alpha = w_0 = 4/9 gives c_s^2 = 1/3)
+  const double xi = p.lattice == CG_D2Q9 ? 3.0 / 5.0 : 9.0 / 19.0;
   ph.rho_r0 = T(p.rho_r0);
   ph.rho_b0 = T(p.rho_b0);
   ph.inv_rho_r0 = T(1.0 / p.rho_r0);

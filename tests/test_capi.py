@@ -60,7 +60,7 @@ def test_defaults_and_workspace(cg):
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("rho_r0", 0.0), ("alpha_b", 1.0),
                                          ("nu_r", -1.0), ("model", 7), ("force_mode", 9),
-                                         ("precision", 5), ("reserved_", 1)])
+                                         ("precision", 5), ("lattice", 2)])
 def test_invalid_params_rejected(cg, field, value):
     p = cg.cg_params_default(8, 8, 8)
     setattr(p, field, value)
@@ -133,3 +133,15 @@ def test_wall_kinds_validated(cg):
         cg.cg_workspace_bytes(cg.make_params(8, 8, 2, bc=(0, 0, cg.CG_BC_SLIP)))
     with pytest.raises(cg.CGError):
         cg.cg_workspace_bytes(cg.make_params(8, 8, 8, bc=(0, 4, 0)))
+
+
+def test_d2q9_parameters_validated(cg):
+    p = cg.make_params(16, 8, 1, lattice=cg.CG_D2Q9, bc=(0, 1, 0))
+    assert cg.cg_workspace_bytes(p) > 0
+    for bad in (dict(nz=2), dict(bc=(0, 0, 1)), dict(bc=(2, 0, 0)), dict(model=cg.CG_MODEL_A),
+                dict(precision="f16s"), dict(solid_mask=1)):
+        kw = dict(lattice=cg.CG_D2Q9)
+        kw.update(bad)
+        nz = kw.pop("nz", 1)
+        with pytest.raises(cg.CGError):
+            cg.cg_workspace_bytes(cg.make_params(16, 8, nz, **kw))

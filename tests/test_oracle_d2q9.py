@@ -1,0 +1,123 @@
+"""Pins of the D2Q9 oracle (App. A) -- CPU only."""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from conftest import load_golden
+
+
+def test_d2q9_lattice_matches_printed_table(orc):
+    c, w = orc.lattice2d()
+    rows = load_golden("d2q9_velocities.txt")
+    for r in rows:
+        i = int(r[0])
+        assert (c[i, 0], c[i, 1]) == (int(r[1]), int(r[2]))
+        assert w[i] == pytest.approx(float(Fraction(r[3])), abs=1e-16)
+    assert abs(w.sum() - 1.0) < 1e-15
+    # second-order isotropy with c_s^2 = 1/3
+    for a in range(2):
+        for b in range(2):
+            assert abs((w * c[:, a] * c[:, b]).sum() - (1.0 / 3.0 if a == b else 0.0)) < 1e-15
+
+
+def test_d2q9_equilibrium_moments_match_appendix_closed_forms(orc):
+    """Central moments of the generalized equilibria of App. A, by the defining
+    sums: k00 = rho, k20 = k02 = p, k22 = p c_s^2, every other one 0."""
+    rng = np.random.default_rng(7)
+    for _ in range(2000):
+        rho = rng.uniform(0.3, 3.0)
+        p = rng.uniform(0.01, 1.0)
+        u = rng.uniform(-0.15, 0.15, 2)
+        k = orc.central_moments2d(orc.feq2d(rho, p, u), u)
+        expect = np.array([rho, 0, p, 0, 0, 0, p, 0, p / 3.0])
+        assert np.abs(k - expect).max() < 2e-15 * max(1.0, rho)
+
+
+def test_d2q9_single_phase_reduces_to_hermite_fourth_order(orc):
+    """With p = rho c_s^2 the generalized equilibria are g^{eq,4}: zeroth to
+    second raw moments rho, rho u, rho u u + p I (textbook)."""
+    c, w = orc.lattice2d()
+    rho, u = 1.3, np.array([0.07, -0.04])
+    f = orc.feq2d(rho, rho / 3.0, u)
+    assert abs(f.sum() - rho) < 1e-15
+    assert np.allclose((f[:, None] * c).sum(0), rho * u, atol=1e-16)
+    m2 = np.einsum("i,ia,ib->ab", f, c, c)
+    assert np.allclose(m2, rho * np.outer(u, u) + rho / 3.0 * np.eye(2), atol=1e-15)
+
+
+def test_d2q9_moment_matrix_inverse(orc):
+    M = orc.moment_matrix2d()
+    Mi = orc.moment_matrix_inverse2d()
+    assert np.abs(M @ Mi - np.eye(9)).max() < 1e-14
+    # tensor product of the textbook 3-point inverse, in the App. A ordering
+    c, _ = orc.lattice2d()
+    inv1 = {-1: (0.0, -0.5, 0.5), 0: (1.0, 0.0, -1.0), 1: (0.0, 0.5, 0.5)}  # f(c) from moments 0, 1, 2
+    for i in range(9):
+        for b in range(3):
+            for a in range(3):
+                assert abs(Mi[i, a + 3 * b] - inv1[c[i, 0]][a] * inv1[c[i, 1]][b]) < 1e-15
+
+
+def test_d2q9_unit_rate_collision_structure(orc):
+    """All omega = 1 except the shear rate: every moment takes its equilibrium
+    value except the first order (F/2), the third order (c_s^2 F/2) and the
+    shear moments; the trace of the diagonal pair carries Q/2."""
+    rng = np.random.default_rng(3)
+    k = rng.normal(size=9)
+    keq = rng.normal(size=9)
+    F, Q = np.array([1e-3, -2e-3]), np.array([3e-4, 5e-4])
+    o1 = 1.7
+    ks = orc.collide_cm2d(k, keq, np.array([1.0, o1, 1.0, 1.0, 1.0]), F, Q)
+    assert ks[0] == k[0]
+    assert ks[1] == pytest.approx(F[0] / 2) and ks[3] == pytest.approx(F[1] / 2)
+    assert ks[4] == pytest.approx((1 - o1) * k[4] + o1 * keq[4])
+    assert ks[2] + ks[6] == pytest.approx(keq[2] + keq[6] + (Q[0] + Q[1]) / 2)
+    assert ks[2] - ks[6] == pytest.approx((1 - o1) * (k[2] - k[6]) + o1 * (keq[2] - keq[6]) + (1 - o1 / 2) * (Q[0] - Q[1]))
+    assert ks[5] == pytest.approx(keq[5] + F[1] / 6) and ks[7] == pytest.approx(keq[7] + F[0] / 6)
+    assert ks[8] == pytest.approx(keq[8])
+
+
+def test_d2q9_mass_conservation_and_uniform_fixed_point(orc):
+    n = 12
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    r = np.sqrt((x - 5.5) ** 2 + (y - 6.5) ** 2)
+    phi0 = np.tanh(2 * (3.5 - r) / 4.0)
+    rr, rb = 2.0 * (1 + phi0) / 2, 1.0 * (1 - phi0) / 2
+    P = orc.make_params2d(n, n, rho_r0=2.0, rho_b0=1.0, alpha_r=1 - (5.0 / 9.0) / 2.0, sigma=0.01)
+    d = orc.Domain2D(P)
+    d.init(rr, rb, np.zeros((2, n, n)) + 0.01)
+    m0 = d.mass()
+    d.step(100)
+    assert np.allclose(d.mass(), m0, rtol=1e-13, atol=0)
+    # a uniform mixture in motion does not change
+    P2 = orc.make_params2d(n, n, sigma=0.0)
+    d2 = orc.Domain2D(P2)
+    u = np.zeros((2, n, n))
+    u[0], u[1] = 0.05, -0.02
+    d2.init(np.full((n, n), 0.4), np.full((n, n), 0.6), u)
+    d2.step(30)
+    m = d2.macros()
+    assert np.abs(m["u"][0] - 0.05).max() < 1e-15 and np.abs(m["u"][1] + 0.02).max() < 1e-15
+
+
+def test_d2q9_oracle_reproduces_the_printed_laplace_row(orc):
+    """First row of the Sec. IV.A table (ratio 1, sigma_th = 0.012, printed
+    sigma_cal = 0.01204, E = 0.30 %): 100 x 100, R = 25, nu = 1/6, beta = 0.7;
+    sigma = R dp at steady state.  The oracle gives 0.012053 (E = 0.44 %)."""
+    n, R, sigma = 100, 25.0, 0.012
+    rows = [r for r in load_golden("laplace_table.txt") if float(r[0]) == 1.0 and float(r[1]) == sigma]
+    s_paper = float(rows[0][2])
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    r = np.sqrt((x - n / 2) ** 2 + (y - n / 2) ** 2)
+    phi0 = np.tanh(2 * (R - r) / 4.0)
+    P = orc.make_params2d(n, n, sigma=sigma, beta=0.7)
+    d = orc.Domain2D(P)
+    d.init((1 + phi0) / 2, (1 - phi0) / 2, np.zeros((2, n, n)))
+    d.step(12000)
+    m = d.macros()
+    Re = math.sqrt(((1 + m["phi"]) / 2).sum() / math.pi)
+    s_cal = (m["p"][r < Re - 5].mean() - m["p"][r > Re + 10].mean()) * Re
+    assert abs(s_cal - s_paper) <= 5e-3 * sigma, (s_cal, s_paper)
+    assert abs(Re - R) < 0.2

@@ -97,6 +97,12 @@ def recorded_traffic(kernel, cells):
     return None
 
 
+def step_slabs(nz, planes=24):
+    """Kernels per pass in one step: the library runs a domain with at least two
+    z slabs of 24 planes as a graph of per-slab kernels (cg27_capi.cu)."""
+    return (nz + planes - 1) // planes if nz >= 2 * planes else 1
+
+
 def workload(edge):
     from paper_2309_07801_gb300 import inputs
     wl = inputs.translating_droplet(edge)
@@ -358,7 +364,7 @@ def run_ours(args, dist):
                        "l2": "inputs larger than L2: populations and recoloring state 2 x %.0f MB" %
                              (N * (27 + 6) * 4 / 1e6)},
             "roofline": roofline, "step_roofline_432B": step_roofline,
-            "e2e": e2e, "gpu_launches": len(cg.PASS_NAMES) * K, "clocks": clk,
+            "e2e": e2e, "gpu_launches": len(cg.PASS_NAMES) * K * step_slabs(wl.nz), "clocks": clk,
             "mass": list(map(float, mass)), "nonfinite": nonfinite}
     if not args.no_serve:
         line["serving"] = serving(args)

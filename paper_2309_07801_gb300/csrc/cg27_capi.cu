@@ -2,6 +2,7 @@
 // workspace layout, kernel launches of one time step, initialisation,
 // read-back, reductions and checkpoints.  Device code is in cg27_device.cuh.
 #include "cg27_host.cuh"
+#include <algorithm>
 #include "cg27_d2q9.cuh"
 
 #include <cmath>
@@ -140,34 +141,137 @@ dim3 grid_of(const cg_params& p, dim3 b) {
   return dim3((p.nx + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, p.nz);
 }
 
+// z slabs of the step graphs: SLAB_PLANES planes in chunks of SLAB_TZ per tile
+// (24 and 8 measured best at 128^3 on GB300 among 14-43 and 7-16)
+constexpr int SLAB_PLANES = 24, SLAB_TZ = 8;
+
+template <typename T, typename SF, bool SOLID>
+void launch_passes(cg_ctx* c, int cur, cudaEvent_t* ev, int zb, int ze) {
+  const Geom g = make_geom(c);
+  const dim3 b(TX, TY, 1);
+  const int tz = std::min(c->tz, ze - zb);
+  const dim3 gr((c->prm.nx + TX - 1) / TX, (c->prm.ny + TY - 1) / TY, (ze - zb + tz - 1) / tz);
+  const dim3 bc = block_of(c->prm);
+  const dim3 gc((c->prm.nx + bc.x - 1) / bc.x, (c->prm.ny + bc.y - 1) / bc.y, ze - zb);
+  const Ptrs<T> P = make_ptrs<T>(c, cur);
+  const Phys<T> ph = make_phys<T>(c->prm);
+  if (ev) cudaEventRecord(ev[0], c->stream);
+  k_macro<T, SF, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph, tz, zb, ze);
+  if (ev) cudaEventRecord(ev[1], c->stream);
+  if constexpr (!SOLID && sizeof(T) == 4)
+    k_fields_sep<T><<<gr, b, 0, c->stream>>>(g, P, ph, tz, zb, ze);
+  else
+    k_fields<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph, tz, zb, ze);
+  if (ev) cudaEventRecord(ev[2], c->stream);
+  k_div_sep<T><<<gr, b, 0, c->stream>>>(g, P, tz, c->prm.use_Q, zb, ze);
+  if (ev) cudaEventRecord(ev[3], c->stream);
+  if (c->unit)
+    k_collide<T, SF, SOLID, true><<<gc, bc, 0, c->stream>>>(g, P, ph, zb);
+  else
+    k_collide<T, SF, SOLID, false><<<gc, bc, 0, c->stream>>>(g, P, ph, zb);
+  if (ev) cudaEventRecord(ev[4], c->stream);
+}
+
+// Slab pipeline of one step: the four passes of each z slab of SLAB_PLANES
+// planes are graph nodes with their true dependencies -- fields(i) after
+// macro(i-1..i+1) (phi with a two-plane halo), div(i) after fields(i-1..i+1),
+// collide(i) after div(i) -- so the passes of different slabs overlap on the
+// GPU (the issue-bound stencil passes with the bandwidth-bound population
+// passes, and the tail of one pass with the head of the next).  One graph per
+// step parity, built on first use.  Results do not depend on the slabs.
+template <typename T, typename SF, bool SOLID>
+cudaGraphExec_t build_slab_graph(cg_ctx* c, int cur) {
+  const int slab = SLAB_PLANES;
+  const int nz = c->prm.nz, ns = (nz + slab - 1) / slab;
+  const Geom g = make_geom(c);
+  const Ptrs<T> P = make_ptrs<T>(c, cur);
+  const Phys<T> ph = make_phys<T>(c->prm);
+  cudaGraph_t gph;
+  cudaGraphCreate(&gph, 0);
+  std::vector<cudaGraphNode_t> M(ns), F(ns), D(ns), C(ns);
+  const dim3 b(TX, TY, 1);
+  const dim3 bc = block_of(c->prm);
+  int use_Q = c->prm.use_Q;
+  auto deps3 = [&](std::vector<cudaGraphNode_t>& v, int i, std::vector<cudaGraphNode_t>& out) {
+    out.clear();
+    for (int d = -1; d <= 1; ++d) {
+      cudaGraphNode_t n = v[(i + d + ns) % ns];
+      if (std::find(out.begin(), out.end(), n) == out.end()) out.push_back(n);
+    }
+  };
+  std::vector<int> zb(ns), ze(ns), tzs(ns);
+  for (int i = 0; i < ns; ++i) {
+    zb[i] = i * slab;
+    ze[i] = std::min(nz, zb[i] + slab);
+    tzs[i] = std::min(SLAB_TZ, ze[i] - zb[i]);
+  }
+  for (int i = 0; i < ns; ++i) {
+    const dim3 gr((c->prm.nx + TX - 1) / TX, (c->prm.ny + TY - 1) / TY, (ze[i] - zb[i] + tzs[i] - 1) / tzs[i]);
+    cudaKernelNodeParams kp = {};
+    void* args[] = {(void*)&g, (void*)&P, (void*)&ph, (void*)&tzs[i], (void*)&zb[i], (void*)&ze[i]};
+    kp.func = (void*)k_macro<T, SF, SOLID>;
+    kp.gridDim = gr;
+    kp.blockDim = b;
+    kp.kernelParams = args;
+    cudaGraphAddKernelNode(&M[i], gph, nullptr, 0, &kp);
+  }
+  std::vector<cudaGraphNode_t> dv;
+  for (int i = 0; i < ns; ++i) {
+    const dim3 gr((c->prm.nx + TX - 1) / TX, (c->prm.ny + TY - 1) / TY, (ze[i] - zb[i] + tzs[i] - 1) / tzs[i]);
+    cudaKernelNodeParams kp = {};
+    void* args[] = {(void*)&g, (void*)&P, (void*)&ph, (void*)&tzs[i], (void*)&zb[i], (void*)&ze[i]};
+    if constexpr (!SOLID && sizeof(T) == 4) kp.func = (void*)k_fields_sep<T>;
+    else kp.func = (void*)k_fields<T, SOLID>;
+    kp.gridDim = gr;
+    kp.blockDim = b;
+    kp.kernelParams = args;
+    deps3(M, i, dv);
+    cudaGraphAddKernelNode(&F[i], gph, dv.data(), dv.size(), &kp);
+  }
+  for (int i = 0; i < ns; ++i) {
+    const dim3 gr((c->prm.nx + TX - 1) / TX, (c->prm.ny + TY - 1) / TY, (ze[i] - zb[i] + tzs[i] - 1) / tzs[i]);
+    cudaKernelNodeParams kp = {};
+    void* args[] = {(void*)&g, (void*)&P, (void*)&tzs[i], (void*)&use_Q, (void*)&zb[i], (void*)&ze[i]};
+    kp.func = (void*)k_div_sep<T>;
+    kp.gridDim = gr;
+    kp.blockDim = b;
+    kp.kernelParams = args;
+    deps3(F, i, dv);
+    cudaGraphAddKernelNode(&D[i], gph, dv.data(), dv.size(), &kp);
+  }
+  for (int i = 0; i < ns; ++i) {
+    const dim3 gc((c->prm.nx + bc.x - 1) / bc.x, (c->prm.ny + bc.y - 1) / bc.y, ze[i] - zb[i]);
+    cudaKernelNodeParams kp = {};
+    void* args[] = {(void*)&g, (void*)&P, (void*)&ph, (void*)&zb[i]};
+    kp.func = c->unit ? (void*)k_collide<T, SF, SOLID, true> : (void*)k_collide<T, SF, SOLID, false>;
+    kp.gridDim = gc;
+    kp.blockDim = bc;
+    kp.kernelParams = args;
+    cudaGraphAddKernelNode(&C[i], gph, &D[i], 1, &kp);
+  }
+  cudaGraphExec_t ex = nullptr;
+  if (cudaGraphInstantiate(&ex, gph, 0) != cudaSuccess) ex = nullptr;
+  cudaGraphDestroy(gph);
+  return ex;
+}
+
 template <typename T, typename SF, bool SOLID>
 void enqueue_step(cg_ctx* c) {
   const int cur = (int)(c->steps & 1);
-  const Geom g = make_geom(c);
-  const dim3 b(TX, TY, 1);
-  const dim3 gr((c->prm.nx + TX - 1) / TX, (c->prm.ny + TY - 1) / TY, (c->prm.nz + c->tz - 1) / c->tz);
-  const dim3 bc = block_of(c->prm), gc = grid_of(c->prm, bc);
-  const Ptrs<T> P = make_ptrs<T>(c, cur);
-  const Phys<T> ph = make_phys<T>(c->prm);
   cudaEvent_t* ev = nullptr;
   if (c->prof_used < c->prof_capacity) ev = &c->events[NUM_EVENTS_PER_STEP * c->prof_used++];
-  if (ev) cudaEventRecord(ev[0], c->stream);
-  k_macro<T, SF, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph, c->tz);
-  if (ev) cudaEventRecord(ev[1], c->stream);
-  // FP32 wall-free domains use the separable stencils; FP64 (shared memory)
-  // and walls (neighbour substitution) use the direct ones
-  if constexpr (!SOLID && sizeof(T) == 4)
-    k_fields_sep<T><<<gr, b, 0, c->stream>>>(g, P, ph, c->tz);
-  else
-    k_fields<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph, c->tz);
-  if (ev) cudaEventRecord(ev[2], c->stream);
-  k_div_sep<T><<<gr, b, 0, c->stream>>>(g, P, c->tz, c->prm.use_Q);
-  if (ev) cudaEventRecord(ev[3], c->stream);
-  if (c->unit)
-    k_collide<T, SF, SOLID, true><<<gc, bc, 0, c->stream>>>(g, P, ph);
-  else
-    k_collide<T, SF, SOLID, false><<<gc, bc, 0, c->stream>>>(g, P, ph);
-  if (ev) cudaEventRecord(ev[4], c->stream);
+  // the slab graphs when the domain has at least two slabs, no per-pass
+  // timing is requested and the stream is not being captured by the caller
+  if (!ev && c->prm.nz >= 2 * SLAB_PLANES && c->slab_ok) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+      if (!c->sgraph[cur]) c->sgraph[cur] = build_slab_graph<T, SF, SOLID>(c, cur);
+      if (c->sgraph[cur] && cudaGraphLaunch(c->sgraph[cur], c->stream) == cudaSuccess) return;
+      (void)cudaGetLastError();
+      c->slab_ok = false;  // graphs unavailable here: plain launches from now on
+    }
+  }
+  launch_passes<T, SF, SOLID>(c, cur, ev, 0, c->prm.nz);
 }
 
 // one D2Q9 step: five per-cell kernels (the normal and force kernels are

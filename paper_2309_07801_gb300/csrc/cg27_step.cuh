@@ -85,8 +85,8 @@ __device__ __forceinline__ int zoff(const Geom& g, int z) { return wrapi(z, g.nz
 // ---- pass 1 -----------------------------------------------------------------------------
 
 template <typename T, typename SF, bool SOLID>
-__device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, const Phys<T>& ph, int tz,
-                                           int bx, int by, int bz) {
+__device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, const Phys<T>& ph, int z0, int z1,
+                                           int bx, int by) {
   using HS = HaloSlots<1>;
   constexpr int W = HS::W, PL = HS::PL;
   constexpr int NS = 2;  // the colour fractions of the source cells
@@ -95,7 +95,6 @@ __device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, cons
   constexpr int RING = 4;
   __shared__ T sS[RING][NS][PL];
   const Col c = make_col(g, bx, by);
-  const int z0 = bz * tz, z1 = min(g.nz, z0 + tz);
   const long long S = g.stride;
   HS hs;
   hs.init(g, c);
@@ -175,8 +174,8 @@ __device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, cons
 // ---- pass 2 -----------------------------------------------------------------------------
 
 template <typename T, bool SOLID>
-__device__ __forceinline__ void fields_tile(const Geom& g, const Ptrs<T>& P, const Phys<T>& ph, int tz,
-                                            int bx, int by, int bz) {
+__device__ __forceinline__ void fields_tile(const Geom& g, const Ptrs<T>& P, const Phys<T>& ph, int z0, int z1,
+                                            int bx, int by) {
   using H2 = HaloSlots<2>;  // phi, 2-cell halo
   using H1 = HaloSlots<1>;  // n, 1-cell halo
   constexpr int W2 = H2::W, P2 = H2::PL, W1 = H1::W, P1 = H1::PL;
@@ -184,7 +183,6 @@ __device__ __forceinline__ void fields_tile(const Geom& g, const Ptrs<T>& P, con
   __shared__ T sN[3][3][P1];  // n of three planes (ring3)
   __shared__ T sG[2][3][NT];  // grad phi of the tile cells, planes of parity 0 and 1
   const Col c = make_col(g, bx, by);
-  const int z0 = bz * tz, z1 = min(g.nz, z0 + tz);
   const long long S = g.stride;
   H2 h2;
   h2.init(g, c);
@@ -358,8 +356,8 @@ __device__ __forceinline__ void fields_tile(const Geom& g, const Ptrs<T>& P, con
 // thread stages A, B for exactly the positions it loaded or computed itself, so
 // no extra barrier is needed.
 template <typename T>
-__device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P, const Phys<T>& ph, int tz,
-                                                int bx, int by, int bz) {
+__device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P, const Phys<T>& ph, int z0,
+                                                int z1, int bx, int by) {
   using H2 = HaloSlots<2>;
   using H1 = HaloSlots<1>;
   constexpr int W2 = H2::W, P2 = H2::PL, W1 = H1::W, P1 = H1::PL;
@@ -370,7 +368,6 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
   __shared__ T sNA[3][P1], sNB[3][P1];  // S_z n_b and D_z n_b of the output plane
   __shared__ T sG[2][3][NT];
   const Col c = make_col(g, bx, by);
-  const int z0 = bz * tz, z1 = min(g.nz, z0 + tz);
   const long long S = g.stride;
   H2 h2;
   h2.init(g, c);
@@ -534,14 +531,13 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
 // components, D_z for the z component) of the output plane in shared memory
 // (two buffers, one barrier per plane).
 template <typename T>
-__device__ __forceinline__ void div_sep_tile(const Geom& g, const Ptrs<T>& P, int tz, int use_Q, int bx, int by,
-                                             int bz) {
+__device__ __forceinline__ void div_sep_tile(const Geom& g, const Ptrs<T>& P, int z0, int z1, int use_Q, int bx,
+                                             int by) {
   using HS = HaloSlots<1>;
   constexpr int W = HS::W, PL = HS::PL, K = HS::K;
   constexpr T S0 = T(2) / T(3), S1 = T(1) / T(6);
   __shared__ T sA[2][6][PL];
   const Col c = make_col(g, bx, by);
-  const int z0 = bz * tz, z1 = min(g.nz, z0 + tz);
   const long long S = g.stride;
   HS hs;
   hs.init(g, c);
@@ -698,35 +694,42 @@ __device__ __forceinline__ void collide_cell(const Geom& g, const Ptrs<T>& P, co
 }
 
 // ---- kernels of one domain ------------------------------------------------------------------
-// Grid (tiles in x, tiles in y, z chunks of tz planes) of TX x TY blocks for the
-// z-marching passes; one thread per cell, one z plane per blockIdx.z, for the
-// collision.
+// Planes zb <= z < ze of the domain (a z slab, or the whole domain): grid (tiles
+// in x, tiles in y, chunks of tz planes) of TX x TY blocks for the z-marching
+// passes; one thread per cell, one z plane per blockIdx.z, for the collision.
 
 template <typename T, typename SF, bool SOLID>
 __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !SOLID) ? 4 : 1)
-    k_macro(Geom g, Ptrs<T> P, Phys<T> ph, int tz) {
-  macro_tile<T, SF, SOLID>(g, P, ph, tz, blockIdx.x, blockIdx.y, blockIdx.z);
+    k_macro(Geom g, Ptrs<T> P, Phys<T> ph, int tz, int zb, int ze) {
+  const int z0 = zb + blockIdx.z * tz;
+  macro_tile<T, SF, SOLID>(g, P, ph, z0, min(ze, z0 + tz), blockIdx.x, blockIdx.y);
 }
 
 template <typename T, bool SOLID>
-__global__ void __launch_bounds__(NT) k_fields(Geom g, Ptrs<T> P, Phys<T> ph, int tz) {
-  fields_tile<T, SOLID>(g, P, ph, tz, blockIdx.x, blockIdx.y, blockIdx.z);
+__global__ void __launch_bounds__(NT) k_fields(Geom g, Ptrs<T> P, Phys<T> ph, int tz, int zb, int ze) {
+  const int z0 = zb + blockIdx.z * tz;
+  fields_tile<T, SOLID>(g, P, ph, z0, min(ze, z0 + tz), blockIdx.x, blockIdx.y);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT) k_fields_sep(Geom g, Ptrs<T> P, Phys<T> ph, int tz) {
-  fields_sep_tile<T>(g, P, ph, tz, blockIdx.x, blockIdx.y, blockIdx.z);
+__global__ void __launch_bounds__(NT) k_fields_sep(Geom g, Ptrs<T> P, Phys<T> ph, int tz, int zb, int ze) {
+  const int z0 = zb + blockIdx.z * tz;
+  fields_sep_tile<T>(g, P, ph, z0, min(ze, z0 + tz), blockIdx.x, blockIdx.y);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT) k_div_sep(Geom g, Ptrs<T> P, int tz, int use_Q) {
-  div_sep_tile<T>(g, P, tz, use_Q, blockIdx.x, blockIdx.y, blockIdx.z);
+__global__ void __launch_bounds__(NT) k_div_sep(Geom g, Ptrs<T> P, int tz, int use_Q, int zb, int ze) {
+  const int z0 = zb + blockIdx.z * tz;
+  div_sep_tile<T>(g, P, z0, min(ze, z0 + tz), use_Q, blockIdx.x, blockIdx.y);
 }
 
 template <typename T, typename SF, bool SOLID, bool UNIT>
-__global__ void __launch_bounds__(128, 6) k_collide(Geom g, Ptrs<T> P, Phys<T> ph) {
+__global__ void __launch_bounds__(128, 6) k_collide(Geom g, Ptrs<T> P, Phys<T> ph, int zb) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
   Cell c;
-  if (!make_cell(g, c)) return;
+  make_cell_at(g, x, y, zb + blockIdx.z, c);
   collide_cell<T, SF, SOLID, UNIT>(g, P, ph, c);
 }
 
@@ -765,7 +768,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !SOLID) ? 4 : 1)
     k_macro_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int par) {
   const int4 t = tile_item(items);
   const Dom<T>& D = doms[t.x];
-  macro_tile<T, SF, SOLID>(D.g, D.P[par], D.ph, D.tz, t.y, t.z, t.w);
+  macro_tile<T, SF, SOLID>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
 }
 
 template <typename T, bool SOLID>
@@ -774,9 +777,9 @@ __global__ void __launch_bounds__(NT)
   const int4 t = tile_item(items);
   const Dom<T>& D = doms[t.x];
   if constexpr (!SOLID && sizeof(T) == 4)
-    fields_sep_tile<T>(D.g, D.P[par], D.ph, D.tz, t.y, t.z, t.w);
+    fields_sep_tile<T>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
   else
-    fields_tile<T, SOLID>(D.g, D.P[par], D.ph, D.tz, t.y, t.z, t.w);
+    fields_tile<T, SOLID>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
 }
 
 template <typename T>
@@ -784,7 +787,7 @@ __global__ void __launch_bounds__(NT)
     k_div_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int par) {
   const int4 t = tile_item(items);
   const Dom<T>& D = doms[t.x];
-  div_sep_tile<T>(D.g, D.P[par], D.tz, D.use_Q, t.y, t.z, t.w);
+  div_sep_tile<T>(D.g, D.P[par], t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), D.use_Q, t.y, t.z);
 }
 
 template <typename T, typename SF, bool SOLID, bool UNIT>

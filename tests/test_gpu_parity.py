@@ -302,3 +302,23 @@ def test_invalid_inputs_rejected_before_launch():
         d.step(1)  # not initialised
     with pytest.raises(cg.CGError):
         d.init(*_droplet(params), solid=np.zeros((6, 6, 6), np.uint8))  # no wall workspace
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16s"])
+def test_slab_graph_schedule_is_bitwise_equal_to_plain_launches(prec):
+    """Domains with nz >= 48 step through the slab-pipeline graphs; with per-pass
+    timing on, the same steps run as plain launches.  Same results."""
+    from paper_2309_07801_gb300 import cg
+    wl = inputs.translating_droplet(64)
+    fields = inputs.workload_fields(wl, noise=1e-3, seed=3)
+    out = []
+    for profile in (False, True):
+        d = cg.Domain(cg.make_params(precision=prec, **wl.params()))
+        d.init(*fields)
+        if profile:
+            cg.cg_profile_enable(d.h, 40)
+        d.step(40)
+        out.append(d.macros())
+        d.close()
+    for key in out[0]:
+        assert np.array_equal(out[0][key], out[1][key]), key

@@ -58,13 +58,15 @@ struct cg_ctx {
   // per-pass timing: events[(CG_NUM_PASSES + 1) * s + k] brackets pass k of timed step s
   std::vector<cudaEvent_t> events;
   int64_t prof_capacity = 0, prof_used = 0;
-  // step graphs of the slab pipeline, per step parity (built on first use)
-  cudaGraphExec_t sgraph[2] = {nullptr, nullptr};
+  // graphs of the slab pipeline, [one step | a chain of steps][parity of the
+  // first step], built on first use
+  cudaGraphExec_t sgraph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   bool slab_ok = true;
   ~cg_ctx() {
     for (cudaEvent_t e : events) cudaEventDestroy(e);
-    for (cudaGraphExec_t g : sgraph)
-      if (g) cudaGraphExecDestroy(g);
+    for (auto& row : sgraph)
+      for (cudaGraphExec_t g : row)
+        if (g) cudaGraphExecDestroy(g);
   }
 };
 

@@ -329,16 +329,30 @@ int enqueue_step_any(cg_ctx* c, int64_t remaining) {
   }
 }
 
-// the population buffer not holding the current state: free between steps
-char* scratch_of(const cg_ctx* c) { return c->ws + c->L.f[1 - (int)(c->steps & 1)]; }
+// Device memory free between steps, for staging host transfers: the
+// population buffer the next step writes.  Transfers go through it in chunks
+// of cells, so it may be smaller than what a whole transfer needs (the 16-bit
+// and D2Q9 buffers are).
+struct Stage {
+  char* p;
+  size_t bytes;
+};
+Stage stage_of(const cg_ctx* c) {
+  const Layout& L = c->L;
+  return {c->ws + L.f[1 - (int)(c->steps & 1)], L.nq * (size_t)L.stride * L.pop_elem};
+}
+// cells per chunk when each cell needs `per_cell` bytes of staging
+long long chunk_cells(const Stage& st, size_t per_cell) {
+  return std::max<long long>(1, (long long)(st.bytes / per_cell));
+}
 
 template <typename T, bool SOLID>
-void enqueue_init2(cg_ctx* c, const double* d_in) {
+void enqueue_init2(cg_ctx* c, const double* d_in, long long lo, long long hi) {
   const Geom g = make_geom(c);
   const dim3 b = block_of(c->prm), gr = grid_of(c->prm, b);
   Ptrs<T> P = make_ptrs<T>(c, 1);  // the initial state goes to buffer 0
-  const long long n = c->L.n;
-  k2_init<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, make_phys<T>(c->prm), d_in, d_in + n, d_in + 2 * n, n);
+  k2_init<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, make_phys<T>(c->prm), d_in, lo, hi);
+  if (hi < c->L.n) return;  // walls once every fluid cell is in place
   if constexpr (SOLID) {
     Ptrs<T> W = make_ptrs<T>(c, 0);
     W.f_out = const_cast<void*>(W.f_in);
@@ -348,19 +362,19 @@ void enqueue_init2(cg_ctx* c, const double* d_in) {
 }
 
 template <typename T, typename SF, bool SOLID>
-void enqueue_init(cg_ctx* c, const double* d_in) {
+void enqueue_init(cg_ctx* c, const double* d_in, long long lo, long long hi) {
   const Geom g = make_geom(c);
   const dim3 b = block_of(c->prm), gr = grid_of(c->prm, b);
   // the initial state is written to buffer 0 (read by the first step)
   Ptrs<T> P = make_ptrs<T>(c, 1);
-  const long long n = c->L.n;
-  k_init<T, SF, SOLID><<<gr, b, 0, c->stream>>>(g, P, make_phys<T>(c->prm), d_in, d_in + n, d_in + 2 * n, n);
+  k_init<T, SF, SOLID><<<gr, b, 0, c->stream>>>(g, P, make_phys<T>(c->prm), d_in, lo, hi);
+  if (hi < c->L.n) return;  // walls once every fluid cell is in place
   if constexpr (SOLID) {
     // walls from the fluid cells of the same buffer (read fluid, write solid)
     Ptrs<T> W = make_ptrs<T>(c, 0);
     W.f_out = const_cast<void*>(W.f_in);
     W.aux_out = const_cast<T*>(W.aux_in);
-    k_init_walls<T, SF><<<gr, b, 0, c->stream>>>(g, W, make_phys<T>(c->prm), d_in, d_in + n);
+    k_init_walls<T, SF><<<gr, b, 0, c->stream>>>(g, W, make_phys<T>(c->prm));
   }
 }
 
@@ -518,17 +532,15 @@ int cg_init_fields(cg_ctx* c, const double* rho_r, const double* rho_b, const do
     if (!(std::isfinite(rho_r[i]) && std::isfinite(rho_b[i]) && rho_r[i] >= 0 && rho_b[i] >= 0))
       return fail(CG_ERR_INVALID_ARG, "densities must be finite and >= 0 (cell " + std::to_string(i) + ")");
   }
-  c->steps = 0;  // staging lives in population buffer 1, the state goes to buffer 0
-  char* stage = scratch_of(c);
-  double* d_in = reinterpret_cast<double*>(stage);
-  const size_t dbytes = (size_t)n * sizeof(double);
-  CG_CUDA(cudaMemcpyAsync(d_in, rho_r, dbytes, cudaMemcpyHostToDevice, c->stream));
-  CG_CUDA(cudaMemcpyAsync(d_in + n, rho_b, dbytes, cudaMemcpyHostToDevice, c->stream));
-  CG_CUDA(cudaMemcpyAsync(d_in + 2 * n, u, 3 * dbytes, cudaMemcpyHostToDevice, c->stream));
+  c->steps = 0;  // the state goes to buffer 0, the staging to buffer 1
+  const Stage st = stage_of(c);
+  double* d_in = reinterpret_cast<double*>(st.p);
   const Geom g = make_geom(c);
   const dim3 b = block_of(c->prm), gr = grid_of(c->prm, b);
   if (c->L.solid) {
-    uint8_t* d_solid = reinterpret_cast<uint8_t*>(stage + align_up(5 * dbytes));
+    // the solid flags are staged in the phi field, which the init kernels
+    // write only after the neighbour mask has been built
+    uint8_t* d_solid = reinterpret_cast<uint8_t*>(c->ws + c->L.phi);
     if (solid)
       CG_CUDA(cudaMemcpyAsync(d_solid, solid, (size_t)n, cudaMemcpyHostToDevice, c->stream));
     k_solid_self<<<gr, b, 0, c->stream>>>(g, d_solid, solid ? 1 : 0, c->prm.bc[0] != CG_BC_PERIODIC,
@@ -538,22 +550,33 @@ int cg_init_fields(cg_ctx* c, const double* rho_r, const double* rho_b, const do
     else
       k_solid_mask<<<gr, b, 0, c->stream>>>(g, d_solid, reinterpret_cast<uint32_t*>(c->ws + c->L.mask));
   }
-  if (c->prm.lattice == CG_D2Q9) {
-    if (c->prm.precision == CG_F64) {
-      if (c->L.solid) enqueue_init2<double, true>(c, d_in); else enqueue_init2<double, false>(c, d_in);
-    } else {
-      if (c->L.solid) enqueue_init2<float, true>(c, d_in); else enqueue_init2<float, false>(c, d_in);
+  // chunks of cells: rho_r, rho_b, u_x, u_y, u_z of each chunk staged together
+  const long long chunk = chunk_cells(st, 5 * sizeof(double));
+  for (long long lo = 0; lo < n; lo += chunk) {
+    const long long hi = std::min(n, lo + chunk), m = hi - lo;
+    const size_t mb = (size_t)m * sizeof(double);
+    const double* src[5] = {rho_r + lo, rho_b + lo, u + lo, u + n + lo, u + 2 * n + lo};
+    for (int a = 0; a < 5; ++a)
+      CG_CUDA(cudaMemcpyAsync(d_in + a * m, src[a], mb, cudaMemcpyHostToDevice, c->stream));
+    if (c->prm.lattice == CG_D2Q9) {
+      if (c->prm.precision == CG_F64) {
+        if (c->L.solid) enqueue_init2<double, true>(c, d_in, lo, hi); else enqueue_init2<double, false>(c, d_in, lo, hi);
+      } else {
+        if (c->L.solid) enqueue_init2<float, true>(c, d_in, lo, hi); else enqueue_init2<float, false>(c, d_in, lo, hi);
+      }
+    } else
+    switch (c->prm.precision) {
+      case CG_F64:
+        if (c->L.solid) enqueue_init<double, double, true>(c, d_in, lo, hi);
+        else enqueue_init<double, double, false>(c, d_in, lo, hi);
+        break;
+      case CG_F32:
+        if (c->L.solid) enqueue_init<float, float, true>(c, d_in, lo, hi);
+        else enqueue_init<float, float, false>(c, d_in, lo, hi);
+        break;
+      case CG_F16S: enqueue_init<float, __half, false>(c, d_in, lo, hi); break;
+      default: enqueue_init<float, __nv_bfloat16, false>(c, d_in, lo, hi); break;
     }
-  } else
-  switch (c->prm.precision) {
-    case CG_F64:
-      if (c->L.solid) enqueue_init<double, double, true>(c, d_in); else enqueue_init<double, double, false>(c, d_in);
-      break;
-    case CG_F32:
-      if (c->L.solid) enqueue_init<float, float, true>(c, d_in); else enqueue_init<float, float, false>(c, d_in);
-      break;
-    case CG_F16S: enqueue_init<float, __half, false>(c, d_in); break;
-    default: enqueue_init<float, __nv_bfloat16, false>(c, d_in); break;
   }
   CG_CUDA(cudaMemsetAsync(c->ws + c->L.flag, 0, sizeof(unsigned int), c->stream));
   CG_CUDA(cudaGetLastError());
@@ -582,26 +605,37 @@ int cg_read_macros(cg_ctx* c, double* rho_r, double* rho_b, double* u, double* p
   if (int rc_ = settle(c)) return rc_;
   if (!c->initialised) return fail(CG_ERR_INVALID_ARG, "cg_init_fields() has not been called");
   const long long n = c->L.n;
-  double* d_out = reinterpret_cast<double*>(scratch_of(c));
+  const Stage st = stage_of(c);
+  double* d_out = reinterpret_cast<double*>(st.p);
   const Geom g = make_geom(c);
   const dim3 b = block_of(c->prm), gr = grid_of(c->prm, b);
   const int cur = (int)(c->steps & 1);
-  if (c->prm.precision == CG_F64) {
-    auto P = make_ptrs<double>(c, cur);
-    if (c->L.solid) k_read_macros<double, true><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), d_out, n);
-    else k_read_macros<double, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), d_out, n);
-  } else {
-    auto P = make_ptrs<float>(c, cur);
-    if (c->L.solid) k_read_macros<float, true><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), d_out, n);
-    else k_read_macros<float, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), d_out, n);
+  // chunks of cells, the seven fields of each chunk staged together
+  const long long chunk = chunk_cells(st, 7 * sizeof(double));
+  for (long long lo = 0; lo < n; lo += chunk) {
+    const long long hi = std::min(n, lo + chunk), m = hi - lo;
+    if (c->prm.precision == CG_F64) {
+      auto P = make_ptrs<double>(c, cur);
+      if (c->L.solid)
+        k_read_macros<double, true><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), d_out, lo, hi);
+      else
+        k_read_macros<double, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), d_out, lo, hi);
+    } else {
+      auto P = make_ptrs<float>(c, cur);
+      if (c->L.solid)
+        k_read_macros<float, true><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), d_out, lo, hi);
+      else
+        k_read_macros<float, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), d_out, lo, hi);
+    }
+    CG_CUDA(cudaGetLastError());
+    const size_t mb = (size_t)m * sizeof(double);
+    double* dst[7] = {rho_r ? rho_r + lo : nullptr, rho_b ? rho_b + lo : nullptr,
+                      u ? u + lo : nullptr,         u ? u + n + lo : nullptr,
+                      u ? u + 2 * n + lo : nullptr, p ? p + lo : nullptr,
+                      phi ? phi + lo : nullptr};
+    for (int a = 0; a < 7; ++a)
+      if (dst[a]) CG_CUDA(cudaMemcpyAsync(dst[a], d_out + a * m, mb, cudaMemcpyDeviceToHost, c->stream));
   }
-  CG_CUDA(cudaGetLastError());
-  const size_t db = (size_t)n * sizeof(double);
-  if (rho_r) CG_CUDA(cudaMemcpyAsync(rho_r, d_out, db, cudaMemcpyDeviceToHost, c->stream));
-  if (rho_b) CG_CUDA(cudaMemcpyAsync(rho_b, d_out + n, db, cudaMemcpyDeviceToHost, c->stream));
-  if (u) CG_CUDA(cudaMemcpyAsync(u, d_out + 2 * n, 3 * db, cudaMemcpyDeviceToHost, c->stream));
-  if (p) CG_CUDA(cudaMemcpyAsync(p, d_out + 5 * n, db, cudaMemcpyDeviceToHost, c->stream));
-  if (phi) CG_CUDA(cudaMemcpyAsync(phi, d_out + 6 * n, db, cudaMemcpyDeviceToHost, c->stream));
   CG_CUDA(cudaStreamSynchronize(c->stream));
   return CG_OK;
 }
@@ -611,46 +645,50 @@ int cg_read_populations(cg_ctx* c, double* fr, double* fb) {
   if (int rc_ = settle(c)) return rc_;
   if (!c->initialised) return fail(CG_ERR_INVALID_ARG, "cg_init_fields() has not been called");
   const long long n = c->L.n;
-  double* d_out = reinterpret_cast<double*>(scratch_of(c));
+  const Stage st = stage_of(c);
+  double* d_out = reinterpret_cast<double*>(st.p);
   const Geom g = make_geom(c);
   const dim3 b = block_of(c->prm), gr = grid_of(c->prm, b);
   // the current state sits in buffer `cur`: read it through the "input" pointers
   const int cur = (int)(c->steps & 1);
-  const size_t db = (size_t)n * sizeof(double);
-  for (int i = 0; i < c->L.nq; ++i) {
+  const long long chunk = chunk_cells(st, 2 * sizeof(double));
+  for (int i = 0; i < c->L.nq; ++i)
+  for (long long lo = 0; lo < n; lo += chunk) {
+    const long long hi = std::min(n, lo + chunk), m = hi - lo;
+    const size_t mb = (size_t)m * sizeof(double);
     if (c->prm.lattice == CG_D2Q9) {
       const int q = paper_to_lex2(i);
       if (c->prm.precision == CG_F64) {
         auto P = make_ptrs<double>(c, cur);
-        if (c->L.solid) k2_read_pop<double, true><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + n);
-        else k2_read_pop<double, false><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + n);
+        if (c->L.solid) k2_read_pop<double, true><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + m, lo, hi);
+        else k2_read_pop<double, false><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + m, lo, hi);
       } else {
         auto P = make_ptrs<float>(c, cur);
-        if (c->L.solid) k2_read_pop<float, true><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + n);
-        else k2_read_pop<float, false><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + n);
+        if (c->L.solid) k2_read_pop<float, true><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + m, lo, hi);
+        else k2_read_pop<float, false><<<gr, b, 0, c->stream>>>(g, P, q, d_out, d_out + m, lo, hi);
       }
     } else if (c->prm.precision == CG_F64) {
       const int q = paper_to_lex(i);
       auto P = make_ptrs<double>(c, cur);
-      if (c->L.solid) k_read_pop<double, double, true><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), q, d_out, d_out + n);
-      else k_read_pop<double, double, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), q, d_out, d_out + n);
+      if (c->L.solid) k_read_pop<double, double, true><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), q, d_out, d_out + m, lo, hi);
+      else k_read_pop<double, double, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), q, d_out, d_out + m, lo, hi);
     } else {
       const int q = paper_to_lex(i);
       auto P = make_ptrs<float>(c, cur);
       if (c->prm.precision == CG_F16S)
-        k_read_pop<float, __half, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + n);
+        k_read_pop<float, __half, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + m, lo, hi);
       else if (c->prm.precision == CG_BF16S)
-        k_read_pop<float, __nv_bfloat16, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + n);
+        k_read_pop<float, __nv_bfloat16, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + m, lo, hi);
       else if (c->L.solid)
-        k_read_pop<float, float, true><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + n);
+        k_read_pop<float, float, true><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + m, lo, hi);
       else
-        k_read_pop<float, float, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + n);
+        k_read_pop<float, float, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + m, lo, hi);
     }
     CG_CUDA(cudaGetLastError());
-    if (fr) CG_CUDA(cudaMemcpyAsync(fr + (size_t)i * n, d_out, db, cudaMemcpyDeviceToHost, c->stream));
-    if (fb) CG_CUDA(cudaMemcpyAsync(fb + (size_t)i * n, d_out + n, db, cudaMemcpyDeviceToHost, c->stream));
-    CG_CUDA(cudaStreamSynchronize(c->stream));
+    if (fr) CG_CUDA(cudaMemcpyAsync(fr + (size_t)i * n + lo, d_out, mb, cudaMemcpyDeviceToHost, c->stream));
+    if (fb) CG_CUDA(cudaMemcpyAsync(fb + (size_t)i * n + lo, d_out + m, mb, cudaMemcpyDeviceToHost, c->stream));
   }
+  CG_CUDA(cudaStreamSynchronize(c->stream));
   return CG_OK;
 }
 

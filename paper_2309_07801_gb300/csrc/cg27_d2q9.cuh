@@ -130,12 +130,15 @@ __device__ __forceinline__ void pull_colour2(const Ptrs<T>& P, long long S, int 
 __global__ void k2_solid_mask(Geom g, const uint8_t* solid, uint32_t* mask);
 
 template <typename T, bool SOLID>
-__global__ void __launch_bounds__(128) k2_init(Geom g, Ptrs<T> P, Phys<T> ph, const double* in_rr,
-                                               const double* in_rb, const double* in_u, long long n) {
+__global__ void __launch_bounds__(128) k2_init(Geom g, Ptrs<T> P, Phys<T> ph, const double* in, long long lo,
+                                               long long hi) {
   Cell2 c;
   if (!make_cell2(g, c)) return;
   const long long S = g.stride;
   const int i0 = c.idx;
+  if (i0 < lo || i0 >= hi) return;
+  // the chunk's inputs: rho_r, rho_b, u_x, u_y, u_z, each hi - lo long
+  const long long ci = i0 - lo, m = hi - lo;
   const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
   if (SOLID && ((mask >> SELF_SOLID_BIT) & 1u)) {
     for (int q = 0; q < 9; ++q) {
@@ -148,8 +151,8 @@ __global__ void __launch_bounds__(128) k2_init(Geom g, Ptrs<T> P, Phys<T> ph, co
     P.phi[i0] = T(0);
     return;
   }
-  const T rr = T(in_rr[i0]), rb = T(in_rb[i0]);
-  const T ux = T(in_u[i0]), uy = T(in_u[n + i0]);
+  const T rr = T(in[ci]), rb = T(in[m + ci]);
+  const T ux = T(in[2 * m + ci]), uy = T(in[3 * m + ci]);
   const T rho = rr + rb, p = rr * ph.cr2 + rb * ph.cb2;
   T k[9];
   keq2(rho, p, k);
@@ -366,21 +369,24 @@ __global__ void __launch_bounds__(128) k2_collide(Geom g, Ptrs<T> P, Phys<T> ph)
 
 // two-colour post-collision populations of direction q (read-back, FP64 out)
 template <typename T, bool SOLID>
-__global__ void __launch_bounds__(128) k2_read_pop(Geom g, Ptrs<T> P, int q, double* out_r, double* out_b) {
+__global__ void __launch_bounds__(128) k2_read_pop(Geom g, Ptrs<T> P, int q, double* out_r, double* out_b,
+                                                   long long lo, long long hi) {
   Cell2 c;
   if (!make_cell2(g, c)) return;
   const long long S = g.stride;
   const int i0 = c.idx;
+  if (i0 < lo || i0 >= hi) return;
+  const long long ci = i0 - lo;
   const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
   const T f = ld(fin<T>(P.f_in) + q * S + i0);
   if (SOLID && ((mask >> SELF_SOLID_BIT) & 1u)) {
-    out_r[i0] = double(f);
-    out_b[i0] = double(ld(P.aux_in + q * S + i0));
+    out_r[ci] = double(f);
+    out_b[ci] = double(ld(P.aux_in + q * S + i0));
     return;
   }
   const T t = (W2<T>(q) / Lat<T>::CS2) * (T(CX2(q)) * ld(P.s_in + 2 * S + i0) + T(CY2(q)) * ld(P.s_in + 3 * S + i0));
-  out_r[i0] = double(ld(P.s_in + i0) * f + t);
-  out_b[i0] = double(ld(P.s_in + S + i0) * f - t);
+  out_r[ci] = double(ld(P.s_in + i0) * f + t);
+  out_b[ci] = double(ld(P.s_in + S + i0) * f - t);
 }
 
 }  // namespace cg27

@@ -534,12 +534,15 @@ __global__ void k_solid_self(Geom g, uint8_t* solid, int has_user, int bx, int b
 __global__ void k_solid_mask(Geom g, const uint8_t* solid, uint32_t* mask);
 
 template <typename T, typename SF, bool SOLID>
-__global__ void __launch_bounds__(128) k_init(Geom g, Ptrs<T> P, Phys<T> ph, const double* in_rr,
-                                              const double* in_rb, const double* in_u, long long n) {
+__global__ void __launch_bounds__(128) k_init(Geom g, Ptrs<T> P, Phys<T> ph, const double* in, long long lo,
+                                              long long hi) {
   Cell c;
   if (!make_cell(g, c)) return;
   const long long S = g.stride;
   const int i0 = c.idx;
+  if (i0 < lo || i0 >= hi) return;
+  // the chunk's inputs: rho_r, rho_b, u_x, u_y, u_z, each hi - lo long
+  const long long ci = i0 - lo, m = hi - lo;
   const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
   if (SOLID && ((mask >> SELF_SOLID_BIT) & 1u)) {
     for (int q = 0; q < 27; ++q) {
@@ -554,8 +557,8 @@ __global__ void __launch_bounds__(128) k_init(Geom g, Ptrs<T> P, Phys<T> ph, con
     P.phi[i0] = T(0);
     return;
   }
-  const T rr = T(in_rr[i0]), rb = T(in_rb[i0]);
-  const T u[3] = {T(in_u[i0]), T(in_u[n + i0]), T(in_u[2 * n + i0])};
+  const T rr = T(in[ci]), rb = T(in[m + ci]);
+  const T u[3] = {T(in[2 * m + ci]), T(in[3 * m + ci]), T(in[4 * m + ci])};
   const T rho = rr + rb;
   const T p = rr * ph.cr2 + rb * ph.cb2;
   T k[27];
@@ -582,13 +585,12 @@ __global__ void __launch_bounds__(128) k_init(Geom g, Ptrs<T> P, Phys<T> ph, con
   P.phi[i0] = order_parameter(rr, rb, ph);
 }
 
-// macroscopic fields to FP64: [rho_r][rho_b][u 3][p][phi], each n long
 // Initial content of the wall cells: the wall rule applied to the initial
 // populations of their fluid neighbours (buffer read for fluid cells and
-// written for solid cells only), with the initial colour densities rr_in, rb_in.
+// written for solid cells only), with the initial colour densities that
+// k_init left in mac.
 template <typename T, typename SF>
-__global__ void __launch_bounds__(128) k_init_walls(Geom g, Ptrs<T> P, Phys<T> ph, const double* rr_in,
-                                                    const double* rb_in) {
+__global__ void __launch_bounds__(128) k_init_walls(Geom g, Ptrs<T> P, Phys<T> ph) {
   Cell c;
   if (!make_cell(g, c)) return;
   const long long S = g.stride;
@@ -603,7 +605,7 @@ __global__ void __launch_bounds__(128) k_init_walls(Geom g, Ptrs<T> P, Phys<T> p
     int out;
     if (!((mask >> OPP(q)) & 1u)) {  // the source is fluid
       pull_colour<T, SF, true>(P, S, q, src, mask, fr, fb, ft);
-      out = wall_emit(q, flip, uw, T(rr_in[src]), T(rb_in[src]), fr, fb);
+      out = wall_emit(q, flip, uw, ld(P.mac + src), ld(P.mac + S + src), fr, fb);
     } else {
       out = flip ? reflect_dir(q, flip) : OPP(q);
     }
@@ -612,49 +614,55 @@ __global__ void __launch_bounds__(128) k_init_walls(Geom g, Ptrs<T> P, Phys<T> p
   }
 }
 
+// macroscopic fields to FP64 for the cells lo <= i < hi:
+// [rho_r][rho_b][u 3][p][phi], each hi - lo long
 template <typename T, bool SOLID>
 __global__ void __launch_bounds__(128) k_read_macros(Geom g, Ptrs<T> P, Phys<T> ph, double* out,
-                                                     long long n) {
+                                                     long long lo, long long hi) {
   Cell c;
   if (!make_cell(g, c)) return;
   const long long S = g.stride;
   const int i0 = c.idx;
+  if (i0 < lo || i0 >= hi) return;
+  const long long ci = i0 - lo, m = hi - lo;
   const T rr = P.mac[i0], rb = P.mac[S + i0];
-  out[i0] = double(rr);
-  out[n + i0] = double(rb);
+  out[ci] = double(rr);
+  out[m + ci] = double(rb);
   const bool solid = SOLID && ((ld(P.mask + i0) >> SELF_SOLID_BIT) & 1u);
   if (solid) {
-    for (int a = 0; a < 5; ++a) out[(2 + a) * n + i0] = 0.0;
+    for (int a = 0; a < 5; ++a) out[(2 + a) * m + ci] = 0.0;
     return;
   }
   const T rho = rr + rb;
   for (int a = 0; a < 3; ++a)
-    out[(2 + a) * n + i0] = double((P.mac[(2 + a) * S + i0] + P.force[a * S + i0] / T(2)) / rho);
-  out[5 * n + i0] = double(rr * ph.cr2 + rb * ph.cb2);
-  out[6 * n + i0] = double(order_parameter(rr, rb, ph));
+    out[(2 + a) * m + ci] = double((P.mac[(2 + a) * S + i0] + P.force[a * S + i0] / T(2)) / rho);
+  out[5 * m + ci] = double(rr * ph.cr2 + rb * ph.cb2);
+  out[6 * m + ci] = double(order_parameter(rr, rb, ph));
 }
 
 // two-colour post-collision populations of lattice direction q to FP64
 template <typename T, typename SF, bool SOLID>
 __global__ void __launch_bounds__(128) k_read_pop(Geom g, Ptrs<T> P, Phys<T> ph, int q, double* out_r,
-                                                  double* out_b) {
+                                                  double* out_b, long long lo, long long hi) {
   Cell c;
   if (!make_cell(g, c)) return;
   const long long S = g.stride;
   const int i0 = c.idx;
+  if (i0 < lo || i0 >= hi) return;
+  const long long ci = i0 - lo;
   T f = Store<SF>::template get<T>(fin<SF>(P.f_in) + q * S + i0);
   if (Store<SF>::SHIFT) f = pop_decode<true>(q, f, P.s_in[S_REST * S + i0], ph.rest1);
   const bool solid = SOLID && ((ld(P.mask + i0) >> SELF_SOLID_BIT) & 1u);
   if (solid) {
-    out_r[i0] = double(f);
-    out_b[i0] = double(P.aux_in[q * S + i0]);
+    out_r[ci] = double(f);
+    out_b[ci] = double(P.aux_in[q * S + i0]);
     return;
   }
   const T cR = T(CX(q)) * P.s_in[2 * S + i0] + T(CY(q)) * P.s_in[3 * S + i0] +
                T(CZ(q)) * P.s_in[4 * S + i0];
   const T t = (q == REST) ? T(0) : (WQ<T>(q) / Lat<T>::CS2) * cR;
-  out_r[i0] = double(P.s_in[i0] * f + t);
-  out_b[i0] = double(P.s_in[S + i0] * f - t);
+  out_r[ci] = double(P.s_in[i0] * f + t);
+  out_b[ci] = double(P.s_in[S + i0] * f - t);
 }
 
 // FP64 block partial sums of rho_r and rho_b in a fixed order

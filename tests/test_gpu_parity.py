@@ -324,3 +324,55 @@ def test_slab_graph_schedule_is_bitwise_equal_to_plain_launches(prec):
         d.close()
     for key in out[0]:
         assert np.array_equal(out[0][key], out[1][key]), key
+
+
+def _readback_runs(make, fields):
+    """The same 16 steps with and without host read-backs in between (after
+    odd and even step counts); returns the final macroscopic fields of each."""
+    out = []
+    for with_reads in (False, True):
+        d = make()
+        d.init(*fields)
+        for k in (5, 6, 5):
+            d.step(k)
+            if with_reads:
+                d.macros()
+                d.populations()
+        out.append(d.macros())
+        d.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16s", "bf16s"])
+def test_host_readback_leaves_the_state_untouched(prec):
+    """Reading the macroscopic fields and the populations in the middle of a run
+    stages through free device memory only: the run continues bitwise as if
+    nothing had been read (the 16-bit population buffers are smaller than one
+    whole read-back, which therefore goes in chunks)."""
+    from paper_2309_07801_gb300 import cg
+    wl = inputs.translating_droplet(32)
+    fields = inputs.workload_fields(wl, noise=1e-3, seed=5)
+    a, b = _readback_runs(lambda: cg.Domain(cg.make_params(precision=prec, **wl.params())), fields)
+    for key in a:
+        assert np.array_equal(a[key], b[key]), key
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_host_readback_leaves_the_state_untouched_d2q9(walls):
+    """As above for the D2Q9 lattice in FP32, whose population buffer holds
+    36 bytes per cell against the 56 of a macroscopic read-back."""
+    from paper_2309_07801_gb300 import cg
+    n = 40
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    phi = np.tanh(2.0 * (9.0 - np.sqrt((x - n / 2) ** 2 + (y - n / 2) ** 2)) / 4.0)
+    rr = (0.5 * (1 + phi))[None]
+    rb = (0.05 * (1 - phi))[None]
+    u = np.zeros((3, 1, n, n))
+    u[0] = 0.01
+    bc = (0, 1, 0) if walls else (0, 0, 0)
+    make = lambda: cg.Domain(cg.make_params(n, n, 1, lattice=cg.CG_D2Q9, precision="f32", bc=bc,
+                                            rho_r0=1.0, rho_b0=0.1, nu_r=0.1, nu_b=0.1, sigma=0.005,
+                                            beta=0.7))
+    a, b = _readback_runs(make, (rr, rb, u))
+    for key in a:
+        assert np.array_equal(a[key], b[key]), key

@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define CG27_ABI_VERSION 2
+#define CG27_ABI_VERSION 3
 
 /* return codes */
 #define CG_OK 0
@@ -96,6 +96,17 @@ extern "C" {
                       at most 159 million cells (27 * cells < 2^32) only */
 #define CG_BF16S 3 /* as CG_F16S with BF16 storage */
 
+/* where the populations live between the collision and the next step's pull
+ * (the paper streams between two copies, Sec. II):
+ *   TWO_BUFFERS  two copies; a step pulls from one and writes the other
+ *   IN_PLACE     one copy, updated in place in two alternating phases (the AA
+ *                pattern): even steps read and write each cell's own slots
+ *                with the directions reversed, odd steps read and write the
+ *                neighbours' slots.  Half the population memory; results are
+ *                bitwise those of TWO_BUFFERS.  D3Q27 only, not in batches. */
+#define CG_STREAM_TWO_BUFFERS 0
+#define CG_STREAM_IN_PLACE 1
+
 typedef struct cg_params {
   int32_t nx, ny, nz;     /* cells per axis, each >= 1 (>= 3 on a wall axis) */
   int32_t bc[3];          /* CG_BC_* per axis (x, y, z) */
@@ -120,6 +131,8 @@ typedef struct cg_params {
   double wall_u[6][3];    /* velocity of the faces x-, x+, y-, y+, z-, z+ of a
                              CG_BC_MOVING axis (finite; the component normal to
                              the face must be 0); ignored for other kinds */
+  int32_t streaming;      /* CG_STREAM_TWO_BUFFERS (default) or CG_STREAM_IN_PLACE */
+  int32_t reserved0;      /* must be 0 */
 } cg_params;
 
 typedef struct cg_ctx cg_ctx; /* opaque */

@@ -22,6 +22,7 @@ CG_FORCE_NONE, CG_FORCE_CONST, CG_FORCE_GRAVITY, CG_FORCE_BUOYANCY = 0, 1, 2, 3
 CG_MODEL_A, CG_MODEL_B, CG_MODEL_C, CG_MODEL_D = 0, 1, 2, 3
 CG_F64, CG_F32, CG_F16S, CG_BF16S = 0, 1, 2, 3
 CG_D3Q27, CG_D2Q9 = 0, 1
+CG_STREAM_TWO_BUFFERS, CG_STREAM_IN_PLACE = 0, 1
 PRECISIONS = {"f64": CG_F64, "f32": CG_F32, "f16s": CG_F16S, "bf16s": CG_BF16S}
 
 
@@ -43,7 +44,8 @@ class cg_params(ctypes.Structure):
                 ("force_mode", ctypes.c_int32), ("model", ctypes.c_int32),
                 ("use_Q", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("solid_mask", ctypes.c_int32), ("lattice", ctypes.c_int32),
-                ("wall_u", (ctypes.c_double * 3) * 6)]
+                ("wall_u", (ctypes.c_double * 3) * 6),
+                ("streaming", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
 # exported entry points of include/cg27.h: name -> (restype, argtypes)

@@ -310,6 +310,8 @@ int cg_batch_add(cg_batch* b, cg_ctx* c) {
   if (c->batch) return fail(CG_ERR_INVALID_ARG, "the domain is already in a batch");
   if (c->prm.precision != b->precision) return fail(CG_ERR_UNSUPPORTED, "precision differs from the batch's");
   if (c->prm.lattice != CG_D3Q27) return fail(CG_ERR_UNSUPPORTED, "batches hold D3Q27 domains");
+  if (c->prm.streaming != CG_STREAM_TWO_BUFFERS)
+    return fail(CG_ERR_UNSUPPORTED, "batches hold domains with two population buffers");
   if ((int)b->members.size() >= b->max_domains) return fail(CG_ERR_INVALID_ARG, "the batch is full");
   const int solid = has_solid(c) ? 1 : 0, unit = c->unit ? 1 : 0;
   if (!b->members.empty() && (solid != b->solid || unit != b->unit))

@@ -84,6 +84,11 @@ int validate(const cg_params* p) {
       27.0 * (((double)p->nx * p->ny * p->nz + 63) / 64 * 64) >= 4294967296.0)
     return fail(CG_ERR_UNSUPPORTED, "16-bit population storage is limited to 159 million cells");
   if (p->lattice != CG_D3Q27 && p->lattice != CG_D2Q9) return fail(CG_ERR_INVALID_ARG, "unknown lattice");
+  if (p->streaming != CG_STREAM_TWO_BUFFERS && p->streaming != CG_STREAM_IN_PLACE)
+    return fail(CG_ERR_INVALID_ARG, "streaming must be CG_STREAM_TWO_BUFFERS or CG_STREAM_IN_PLACE");
+  if (p->reserved0 != 0) return fail(CG_ERR_INVALID_ARG, "reserved0 must be 0");
+  if (p->streaming == CG_STREAM_IN_PLACE && p->lattice != CG_D3Q27)
+    return fail(CG_ERR_UNSUPPORTED, "in-place streaming is implemented for D3Q27");
   if (p->lattice == CG_D2Q9) {
     if (p->nz != 1) return fail(CG_ERR_INVALID_ARG, "a D2Q9 domain has nz = 1");
     if (p->bc[2] != CG_BC_PERIODIC) return fail(CG_ERR_INVALID_ARG, "a D2Q9 domain has bc[2] = CG_BC_PERIODIC");
@@ -113,10 +118,12 @@ Layout make_layout(const cg_params& p) {
     return at;
   };
   const size_t field = (size_t)L.stride * L.elem;
-  for (int b = 0; b < 2; ++b) L.f[b] = take(L.nq * (size_t)L.stride * L.pop_elem);
+  // in place: one population buffer (and one wall buffer), named twice
+  L.inplace = p.streaming == CG_STREAM_IN_PLACE;
+  for (int b = 0; b < 2; ++b) L.f[b] = (b && L.inplace) ? L.f[0] : take(L.nq * (size_t)L.stride * L.pop_elem);
   for (int b = 0; b < 2; ++b) L.s[b] = take(L.ns * field);
   if (L.solid) {
-    for (int b = 0; b < 2; ++b) L.aux[b] = take(L.nq * field);
+    for (int b = 0; b < 2; ++b) L.aux[b] = (b && L.inplace) ? L.aux[0] : take(L.nq * field);
     L.mask = take((size_t)L.stride * 4);
   }
   L.mac = take(5 * field);
@@ -147,6 +154,22 @@ constexpr int SLAB_PLANES = 24, SLAB_TZ = 8;
 // steps chained in one slab graph (8: +6 % over one step per graph at 128^3)
 constexpr int GRAPH_STEPS = 8;
 
+// the macroscopic pass and the collision of a step of stream mode sm
+template <typename T, typename SF, bool SOLID>
+void* macro_kernel(int sm) {
+  if (sm == SM_EVEN) return (void*)k_macro<T, SF, SOLID, SM_EVEN>;
+  if (sm == SM_ODD) return (void*)k_macro<T, SF, SOLID, SM_ODD>;
+  return (void*)k_macro<T, SF, SOLID, SM_AB>;
+}
+template <typename T, typename SF, bool SOLID>
+void* collide_kernel(int sm, bool unit) {
+  if (sm == SM_EVEN)
+    return unit ? (void*)k_collide<T, SF, SOLID, true, SM_EVEN> : (void*)k_collide<T, SF, SOLID, false, SM_EVEN>;
+  if (sm == SM_ODD)
+    return unit ? (void*)k_collide<T, SF, SOLID, true, SM_ODD> : (void*)k_collide<T, SF, SOLID, false, SM_ODD>;
+  return unit ? (void*)k_collide<T, SF, SOLID, true, SM_AB> : (void*)k_collide<T, SF, SOLID, false, SM_AB>;
+}
+
 template <typename T, typename SF, bool SOLID>
 void launch_passes(cg_ctx* c, int cur, cudaEvent_t* ev, int zb, int ze) {
   const Geom g = make_geom(c);
@@ -157,8 +180,13 @@ void launch_passes(cg_ctx* c, int cur, cudaEvent_t* ev, int zb, int ze) {
   const dim3 gc((c->prm.nx + bc.x - 1) / bc.x, (c->prm.ny + bc.y - 1) / bc.y, ze - zb);
   const Ptrs<T> P = make_ptrs<T>(c, cur);
   const Phys<T> ph = make_phys<T>(c->prm);
+  const int sm = next_mode(c->L.inplace, cur);
   if (ev) cudaEventRecord(ev[0], c->stream);
-  k_macro<T, SF, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph, tz, zb, ze);
+  {
+    int tz_ = tz;
+    void* args[] = {(void*)&g, (void*)&P, (void*)&ph, (void*)&tz_, (void*)&zb, (void*)&ze};
+    cudaLaunchKernel(macro_kernel<T, SF, SOLID>(sm), gr, b, args, 0, c->stream);
+  }
   if (ev) cudaEventRecord(ev[1], c->stream);
   if constexpr (!SOLID && sizeof(T) == 4)
     k_fields_sep<T><<<gr, b, 0, c->stream>>>(g, P, ph, tz, zb, ze);
@@ -167,10 +195,10 @@ void launch_passes(cg_ctx* c, int cur, cudaEvent_t* ev, int zb, int ze) {
   if (ev) cudaEventRecord(ev[2], c->stream);
   k_div_sep<T><<<gr, b, 0, c->stream>>>(g, P, tz, c->prm.use_Q, zb, ze);
   if (ev) cudaEventRecord(ev[3], c->stream);
-  if (c->unit)
-    k_collide<T, SF, SOLID, true><<<gc, bc, 0, c->stream>>>(g, P, ph, zb);
-  else
-    k_collide<T, SF, SOLID, false><<<gc, bc, 0, c->stream>>>(g, P, ph, zb);
+  {
+    void* args[] = {(void*)&g, (void*)&P, (void*)&ph, (void*)&zb};
+    cudaLaunchKernel(collide_kernel<T, SF, SOLID>(sm, c->unit), gc, bc, args, 0, c->stream);
+  }
   if (ev) cudaEventRecord(ev[4], c->stream);
 }
 
@@ -225,11 +253,12 @@ cudaGraphExec_t build_slab_graph(cg_ctx* c, int cur0, int nsteps) {
   std::vector<cudaGraphNode_t> dv;
   for (int s = 0; s < nsteps && ok; ++s) {
     const Ptrs<T>& Pc = P[(cur0 + s) & 1];
+    const int sm = next_mode(c->L.inplace, cur0 + s);
     for (int i = 0; i < ns; ++i) {
       const dim3 gr((c->prm.nx + TX - 1) / TX, (c->prm.ny + TY - 1) / TY, (ze[i] - zb[i] + tzs[i] - 1) / tzs[i]);
       void* args[] = {(void*)&g, (void*)&Pc, (void*)&ph, (void*)&tzs[i], (void*)&zb[i], (void*)&ze[i]};
       if (s > 0) deps3(Cprev, i, dv); else dv.clear();
-      add(&M[i], (void*)k_macro<T, SF, SOLID>, gr, b, args, dv);
+      add(&M[i], macro_kernel<T, SF, SOLID>(sm), gr, b, args, dv);
     }
     for (int i = 0; i < ns; ++i) {
       const dim3 gr((c->prm.nx + TX - 1) / TX, (c->prm.ny + TY - 1) / TY, (ze[i] - zb[i] + tzs[i] - 1) / tzs[i]);
@@ -250,8 +279,7 @@ cudaGraphExec_t build_slab_graph(cg_ctx* c, int cur0, int nsteps) {
       const dim3 gc((c->prm.nx + bc.x - 1) / bc.x, (c->prm.ny + bc.y - 1) / bc.y, ze[i] - zb[i]);
       void* args[] = {(void*)&g, (void*)&Pc, (void*)&ph, (void*)&zb[i]};
       dv.assign(1, D[i]);
-      add(&C[i], c->unit ? (void*)k_collide<T, SF, SOLID, true> : (void*)k_collide<T, SF, SOLID, false>, gc, bc,
-          args, dv);
+      add(&C[i], collide_kernel<T, SF, SOLID>(sm, c->unit), gc, bc, args, dv);
     }
     Cprev = C;
   }
@@ -330,16 +358,18 @@ int enqueue_step_any(cg_ctx* c, int64_t remaining) {
 }
 
 // Device memory free between steps, for staging host transfers: the
-// population buffer the next step writes.  Transfers go through it in chunks
-// of cells, so it may be smaller than what a whole transfer needs (the 16-bit
-// and D2Q9 buffers are).
+// population buffer the next step writes, or with in-place streaming the
+// recoloring-state buffer the next step writes.  Transfers go through it in
+// chunks of cells, so it may be smaller than what a whole transfer needs.
 struct Stage {
   char* p;
   size_t bytes;
 };
 Stage stage_of(const cg_ctx* c) {
   const Layout& L = c->L;
-  return {c->ws + L.f[1 - (int)(c->steps & 1)], L.nq * (size_t)L.stride * L.pop_elem};
+  const int spare = 1 - (int)(c->steps & 1);
+  if (L.inplace) return {c->ws + L.s[spare], L.ns * (size_t)L.stride * L.elem};
+  return {c->ws + L.f[spare], L.nq * (size_t)L.stride * L.pop_elem};
 }
 // cells per chunk when each cell needs `per_cell` bytes of staging
 long long chunk_cells(const Stage& st, size_t per_cell) {
@@ -367,14 +397,17 @@ void enqueue_init(cg_ctx* c, const double* d_in, long long lo, long long hi) {
   const dim3 b = block_of(c->prm), gr = grid_of(c->prm, b);
   // the initial state is written to buffer 0 (read by the first step)
   Ptrs<T> P = make_ptrs<T>(c, 1);
-  k_init<T, SF, SOLID><<<gr, b, 0, c->stream>>>(g, P, make_phys<T>(c->prm), d_in, lo, hi);
+  // laid out as if an odd step had written it (in place) or in buffer 0
+  k_init<T, SF, SOLID><<<gr, b, 0, c->stream>>>(g, P, make_phys<T>(c->prm), d_in, lo, hi,
+                                                last_mode(c->L.inplace, 0));
   if (hi < c->L.n) return;  // walls once every fluid cell is in place
   if constexpr (SOLID) {
     // walls from the fluid cells of the same buffer (read fluid, write solid)
     Ptrs<T> W = make_ptrs<T>(c, 0);
     W.f_out = const_cast<void*>(W.f_in);
     W.aux_out = const_cast<T*>(W.aux_in);
-    k_init_walls<T, SF><<<gr, b, 0, c->stream>>>(g, W, make_phys<T>(c->prm));
+    k_init_walls<T, SF><<<gr, b, 0, c->stream>>>(g, W, make_phys<T>(c->prm), next_mode(c->L.inplace, 0),
+                                                 last_mode(c->L.inplace, 0));
   }
 }
 
@@ -652,6 +685,7 @@ int cg_read_populations(cg_ctx* c, double* fr, double* fb) {
   // the current state sits in buffer `cur`: read it through the "input" pointers
   const int cur = (int)(c->steps & 1);
   const long long chunk = chunk_cells(st, 2 * sizeof(double));
+  const int sm = last_mode(c->L.inplace, c->steps);  // where the last step left the populations
   for (int i = 0; i < c->L.nq; ++i)
   for (long long lo = 0; lo < n; lo += chunk) {
     const long long hi = std::min(n, lo + chunk), m = hi - lo;
@@ -670,19 +704,19 @@ int cg_read_populations(cg_ctx* c, double* fr, double* fb) {
     } else if (c->prm.precision == CG_F64) {
       const int q = paper_to_lex(i);
       auto P = make_ptrs<double>(c, cur);
-      if (c->L.solid) k_read_pop<double, double, true><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), q, d_out, d_out + m, lo, hi);
-      else k_read_pop<double, double, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), q, d_out, d_out + m, lo, hi);
+      if (c->L.solid) k_read_pop<double, double, true><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), q, d_out, d_out + m, lo, hi, sm);
+      else k_read_pop<double, double, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), q, d_out, d_out + m, lo, hi, sm);
     } else {
       const int q = paper_to_lex(i);
       auto P = make_ptrs<float>(c, cur);
       if (c->prm.precision == CG_F16S)
-        k_read_pop<float, __half, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + m, lo, hi);
+        k_read_pop<float, __half, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + m, lo, hi, sm);
       else if (c->prm.precision == CG_BF16S)
-        k_read_pop<float, __nv_bfloat16, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + m, lo, hi);
+        k_read_pop<float, __nv_bfloat16, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + m, lo, hi, sm);
       else if (c->L.solid)
-        k_read_pop<float, float, true><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + m, lo, hi);
+        k_read_pop<float, float, true><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + m, lo, hi, sm);
       else
-        k_read_pop<float, float, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + m, lo, hi);
+        k_read_pop<float, float, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), q, d_out, d_out + m, lo, hi, sm);
     }
     CG_CUDA(cudaGetLastError());
     if (fr) CG_CUDA(cudaMemcpyAsync(fr + (size_t)i * n + lo, d_out, mb, cudaMemcpyDeviceToHost, c->stream));
@@ -762,7 +796,7 @@ int cg_steps_taken(cg_ctx* c, int64_t* steps) {
 namespace {
 struct StateHeader {
   char magic[8];
-  int32_t abi, nx, ny, nz, precision, solid;
+  int32_t abi, nx, ny, nz, precision, solid, lattice, streaming;
   int64_t steps;
   uint64_t payload;
 };
@@ -809,6 +843,8 @@ int cg_save_state(cg_ctx* c, void* host, size_t bytes) {
   h.nx = c->prm.nx; h.ny = c->prm.ny; h.nz = c->prm.nz;
   h.precision = c->prm.precision;
   h.solid = c->L.solid;
+  h.lattice = c->prm.lattice;
+  h.streaming = c->prm.streaming;
   h.steps = c->steps;
   h.payload = need - sizeof(StateHeader);
   std::memcpy(host, &h, sizeof(h));
@@ -832,7 +868,7 @@ int cg_load_state(cg_ctx* c, const void* host, size_t bytes) {
   if (std::memcmp(h.magic, "CG27STAT", 8) != 0 || h.abi != CG27_ABI_VERSION)
     return fail(CG_ERR_INVALID_ARG, "not a checkpoint of this library version");
   if (h.nx != c->prm.nx || h.ny != c->prm.ny || h.nz != c->prm.nz || h.precision != c->prm.precision ||
-      h.solid != (int)c->L.solid)
+      h.solid != (int)c->L.solid || h.lattice != c->prm.lattice || h.streaming != c->prm.streaming)
     return fail(CG_ERR_INVALID_ARG, "checkpoint does not match the domain parameters");
   c->steps = h.steps;  // selects the buffer the regions go to
   size_t off[6], len[6];

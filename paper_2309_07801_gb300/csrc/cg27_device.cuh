@@ -218,19 +218,67 @@ __device__ __forceinline__ int nbr(const Cell& c, int dx, int dy, int dz) {
 template <typename T>
 __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 
+// ---- where populations live: two buffers, or one buffer updated in place -------
+// Stream modes of a step.  Two buffers (pull): cell x reads the population of
+// direction q from the input buffer at (q, x - c_q) and writes its
+// post-collision value to the output buffer at (q, x).  In place (one buffer,
+// two alternating phases, the AA pattern):
+//   even step: read (q, x),            write (opp q, x)
+//   odd step:  read (opp q, x - c_q),  write (q, x + c_q)
+// Every location is read and then written by one cell only, within the
+// macroscopic pass and the collision of a step, so the update needs no second
+// buffer, and the read-only load path never meets a location after its write.
+// Between steps the post-collision value of direction q of cell x sits at
+// (q, x + c_q) before an even step and at (opp q, x) before an odd one.
+constexpr int SM_AB = 0, SM_EVEN = 1, SM_ODD = 2;
+template <int SM>
+__host__ __device__ constexpr int rd_dir(int q) { return SM == SM_ODD ? OPP(q) : q; }
+template <int SM>
+__host__ __device__ constexpr int wr_dir(int q) { return SM == SM_EVEN ? OPP(q) : q; }
+// the read cell is x + rd_sign * c_q
+template <int SM>
+__host__ __device__ constexpr int rd_sign() { return SM == SM_EVEN ? 0 : -1; }
+
+// element index of the population of direction q that cell c pulls at a step
+// of mode sm (run-time form, for the kernels outside the step)
+__device__ __forceinline__ long long pull_index(int sm, int q, long long S, const Cell& c) {
+  if (sm == SM_EVEN) return q * S + c.idx;
+  const int src = nbr(c, -CX(q), -CY(q), -CZ(q));
+  return (sm == SM_ODD ? OPP(q) : q) * S + src;
+}
+// element index of the post-collision population of direction q of cell c,
+// as written by a step of mode sm
+__device__ __forceinline__ long long emit_index(int sm, int q, long long S, const Cell& c) {
+  if (sm == SM_EVEN) return OPP(q) * S + c.idx;
+  if (sm == SM_ODD) return q * S + nbr(c, CX(q), CY(q), CZ(q));
+  return q * S + c.idx;
+}
+// stream mode of the step that follows `steps` steps
+__host__ __device__ inline int next_mode(int inplace, long long steps) {
+  return inplace ? ((steps & 1) ? SM_ODD : SM_EVEN) : SM_AB;
+}
+// stream mode of the step that left the state after `steps` steps (the
+// initial state is laid out as if an odd step had written it)
+__host__ __device__ inline int last_mode(int inplace, long long steps) {
+  return inplace ? ((steps & 1) ? SM_EVEN : SM_ODD) : SM_AB;
+}
+
 // ---- pull of one direction with the colour split of Eq. (recoloring) -------------
 
+// q: direction, src: the source cell x - c_q (its recoloring state), pidx: the
+// element index of the population in the buffers (q * stride + src with two
+// buffers)
 template <typename T, typename SF, bool SOLID>
-__device__ __forceinline__ void pull_colour(const Ptrs<T>& P, long long stride, int q, int src,
+__device__ __forceinline__ void pull_colour(const Ptrs<T>& P, long long stride, int q, int src, long long pidx,
                                             uint32_t mask, T& fr, T& fb, T& ft, T ph_rest1 = T(0)) {
   static_assert(!(SOLID && Store<SF>::SHIFT), "walls are not available with 16-bit populations");
-  T f = Store<SF>::template get<T>(fin<SF>(P.f_in) + q * stride + src);
+  T f = Store<SF>::template get<T>(fin<SF>(P.f_in) + pidx);
   if (Store<SF>::SHIFT)
     f = pop_decode<true>(q, f, q == REST ? ld(P.s_in + S_REST * stride + src) : T(0), ph_rest1);
   if (SOLID && ((mask >> OPP(q)) & 1u)) {
     // the source is solid: it stores the red part in F and the blue part in AUX
     fr = f;
-    fb = ld(P.aux_in + q * stride + src);
+    fb = ld(P.aux_in + pidx);
     ft = fr + fb;
   } else {
     const T a = ld(P.s_in + src);
@@ -535,7 +583,7 @@ __global__ void k_solid_mask(Geom g, const uint8_t* solid, uint32_t* mask);
 
 template <typename T, typename SF, bool SOLID>
 __global__ void __launch_bounds__(128) k_init(Geom g, Ptrs<T> P, Phys<T> ph, const double* in, long long lo,
-                                              long long hi) {
+                                              long long hi, int sm) {
   Cell c;
   if (!make_cell(g, c)) return;
   const long long S = g.stride;
@@ -546,8 +594,9 @@ __global__ void __launch_bounds__(128) k_init(Geom g, Ptrs<T> P, Phys<T> ph, con
   const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
   if (SOLID && ((mask >> SELF_SOLID_BIT) & 1u)) {
     for (int q = 0; q < 27; ++q) {
-      fout<SF>(P.f_out)[q * S + i0] = Store<SF>::put(T(0));
-      P.aux_out[q * S + i0] = T(0);
+      const long long o = emit_index(sm, q, S, c);
+      fout<SF>(P.f_out)[o] = Store<SF>::put(T(0));
+      P.aux_out[o] = T(0);
     }
     for (int a = 0; a < 6; ++a) {
       P.s_out[a * S + i0] = T(0);
@@ -567,10 +616,10 @@ __global__ void __launch_bounds__(128) k_init(Geom g, Ptrs<T> P, Phys<T> ph, con
   const T r0 = Store<SF>::SHIFT ? rest_zero(rho, p) : T(0);
 #pragma unroll
   for (int q = 0; q < 27; ++q)
-    fout<SF>(P.f_out)[q * S + i0] =
+    fout<SF>(P.f_out)[emit_index(sm, q, S, c)] =
         Store<SF>::put(pop_encode<Store<SF>::SHIFT>(q, k[q], r0, ph.rest1));
   if (SOLID)
-    for (int q = 0; q < 27; ++q) P.aux_out[q * S + i0] = T(0);
+    for (int q = 0; q < 27; ++q) P.aux_out[emit_index(sm, q, S, c)] = T(0);
   P.s_out[i0] = rr / rho;
   P.s_out[S + i0] = rb / rho;
   P.s_out[2 * S + i0] = P.s_out[3 * S + i0] = P.s_out[4 * S + i0] = T(0);
@@ -590,7 +639,7 @@ __global__ void __launch_bounds__(128) k_init(Geom g, Ptrs<T> P, Phys<T> ph, con
 // written for solid cells only), with the initial colour densities that
 // k_init left in mac.
 template <typename T, typename SF>
-__global__ void __launch_bounds__(128) k_init_walls(Geom g, Ptrs<T> P, Phys<T> ph) {
+__global__ void __launch_bounds__(128) k_init_walls(Geom g, Ptrs<T> P, Phys<T> ph, int sm_in, int sm_out) {
   Cell c;
   if (!make_cell(g, c)) return;
   const long long S = g.stride;
@@ -604,13 +653,14 @@ __global__ void __launch_bounds__(128) k_init_walls(Geom g, Ptrs<T> P, Phys<T> p
     T fr = T(0), fb = T(0), ft;
     int out;
     if (!((mask >> OPP(q)) & 1u)) {  // the source is fluid
-      pull_colour<T, SF, true>(P, S, q, src, mask, fr, fb, ft);
+      pull_colour<T, SF, true>(P, S, q, src, pull_index(sm_in, q, S, c), mask, fr, fb, ft);
       out = wall_emit(q, flip, uw, ld(P.mac + src), ld(P.mac + S + src), fr, fb);
     } else {
       out = flip ? reflect_dir(q, flip) : OPP(q);
     }
-    fout<SF>(P.f_out)[out * S + i0] = Store<SF>::put(fr);
-    P.aux_out[out * S + i0] = fb;
+    const long long o = emit_index(sm_out, out, S, c);
+    fout<SF>(P.f_out)[o] = Store<SF>::put(fr);
+    P.aux_out[o] = fb;
   }
 }
 
@@ -643,19 +693,21 @@ __global__ void __launch_bounds__(128) k_read_macros(Geom g, Ptrs<T> P, Phys<T> 
 // two-colour post-collision populations of lattice direction q to FP64
 template <typename T, typename SF, bool SOLID>
 __global__ void __launch_bounds__(128) k_read_pop(Geom g, Ptrs<T> P, Phys<T> ph, int q, double* out_r,
-                                                  double* out_b, long long lo, long long hi) {
+                                                  double* out_b, long long lo, long long hi, int sm) {
   Cell c;
   if (!make_cell(g, c)) return;
   const long long S = g.stride;
   const int i0 = c.idx;
   if (i0 < lo || i0 >= hi) return;
   const long long ci = i0 - lo;
-  T f = Store<SF>::template get<T>(fin<SF>(P.f_in) + q * S + i0);
+  // sm: the mode of the step that wrote the state
+  const long long o = emit_index(sm, q, S, c);
+  T f = Store<SF>::template get<T>(fin<SF>(P.f_in) + o);
   if (Store<SF>::SHIFT) f = pop_decode<true>(q, f, P.s_in[S_REST * S + i0], ph.rest1);
   const bool solid = SOLID && ((ld(P.mask + i0) >> SELF_SOLID_BIT) & 1u);
   if (solid) {
     out_r[ci] = double(f);
-    out_b[ci] = double(P.aux_in[q * S + i0]);
+    out_b[ci] = double(P.aux_in[o]);
     return;
   }
   const T cR = T(CX(q)) * P.s_in[2 * S + i0] + T(CY(q)) * P.s_in[3 * S + i0] +

@@ -36,6 +36,7 @@ struct Layout {
   int ns = 6;           // fields of the recoloring state
   int nq = 27;          // populations per cell (27 for D3Q27, 9 for D2Q9)
   bool solid = false;
+  bool inplace = false;  // one population buffer (f[1] == f[0]), updated in place
   int red_blocks = 0;
   size_t f[2] = {0, 0}, s[2] = {0, 0}, aux[2] = {0, 0};
   size_t mask = 0, mac = 0, phi = 0, qc = 0, force = 0, wv = 0;

@@ -84,9 +84,10 @@ __device__ __forceinline__ int zoff(const Geom& g, int z) { return wrapi(z, g.nz
 
 // ---- pass 1 -----------------------------------------------------------------------------
 
-template <typename T, typename SF, bool SOLID>
+template <typename T, typename SF, bool SOLID, int SM = SM_AB>
 __device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, const Phys<T>& ph, int z0, int z1,
                                            int bx, int by) {
+  constexpr int RS = rd_sign<SM>();
   using HS = HaloSlots<1>;
   constexpr int W = HS::W, PL = HS::PL;
   constexpr int NS = 2;  // the colour fractions of the source cells
@@ -130,8 +131,8 @@ __device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, cons
       T f[27];
 #pragma unroll
       for (int q = 0; q < 27; ++q)
-        f[q] = Store<SF>::template get<T>(fin<SF>(P.f_in) + q * S +
-                                          (c.xs[1 - CX(q)] + c.ys[1 - CY(q)] + zo[1 - CZ(q)]));
+        f[q] = Store<SF>::template get<T>(fin<SF>(P.f_in) + rd_dir<SM>(q) * S +
+                                          (c.xs[1 + RS * CX(q)] + c.ys[1 + RS * CY(q)] + zo[1 + RS * CZ(q)]));
       const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
       const T s_rest0 = SHIFT ? ld(P.s_in + S_REST * S + i0) : T(0);
       // sum over q of (w_q / c_s^2) c_q . R(x - c_q), from the divergence pass
@@ -144,7 +145,7 @@ __device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, cons
         if (SHIFT) f[q] = pop_decode<true>(q, f[q], s_rest0, ph.rest1);
         T ft = f[q];
         if (SOLID && ((mask >> OPP(q)) & 1u)) {
-          const T fb = ld(P.aux_in + q * S + src);
+          const T fb = ld(P.aux_in + rd_dir<SM>(q) * S + (SM == SM_EVEN ? i0 : src));
           rr += f[q];
           rb += fb;
           ft = f[q] + fb;
@@ -623,8 +624,9 @@ __device__ __forceinline__ long long pop_index(int q, long long S, int i) {
 // (six 128-thread blocks per SM) so that enough warps keep loads in flight; at
 // this occupancy the kernel streams at about the copy bandwidth of the device.
 
-template <typename T, typename SF, bool SOLID, bool UNIT>
+template <typename T, typename SF, bool SOLID, bool UNIT, int SM = SM_AB>
 __device__ __forceinline__ void collide_cell(const Geom& g, const Ptrs<T>& P, const Phys<T>& ph, const Cell& c) {
+  constexpr int RS = rd_sign<SM>();
   constexpr bool SHIFT = Store<SF>::SHIFT;
   const long long S = g.stride;
   const int i0 = c.idx;
@@ -637,19 +639,21 @@ __device__ __forceinline__ void collide_cell(const Geom& g, const Ptrs<T>& P, co
     for (int q = 0; q < 27; ++q) {
       const int src = nbr(c, -CX(q), -CY(q), -CZ(q));
       T fr, fb, ft;
-      pull_colour<T, SF, SOLID>(P, S, q, src, mask, fr, fb, ft);
+      pull_colour<T, SF, SOLID>(P, S, q, src, pull_index(SM, q, S, c), mask, fr, fb, ft);
       const bool fluid_src = !((mask >> OPP(q)) & 1u);
       const int out = wall_emit(q, flip, uw, fluid_src ? ld(P.mac + src) : T(0),
                                 fluid_src ? ld(P.mac + S + src) : T(0), fr, fb);
-      fout<SF>(P.f_out)[out * S + i0] = Store<SF>::put(fr);
-      P.aux_out[out * S + i0] = fb;
+      const long long o = emit_index(SM, out, S, c);
+      fout<SF>(P.f_out)[o] = Store<SF>::put(fr);
+      P.aux_out[o] = fb;
     }
     return;
   }
   T f[27];
 #pragma unroll
   for (int q = 0; q < 27; ++q)
-    f[q] = Store<SF>::template get<T>(fin<SF>(P.f_in) + pop_index<SHIFT>(q, S, nbr(c, -CX(q), -CY(q), -CZ(q))));
+    f[q] = Store<SF>::template get<T>(fin<SF>(P.f_in) +
+                                      pop_index<SHIFT>(rd_dir<SM>(q), S, nbr(c, RS * CX(q), RS * CY(q), RS * CZ(q))));
   if (SHIFT) {
     const T r0 = ld(P.s_in + S_REST * S + i0);
 #pragma unroll
@@ -659,7 +663,7 @@ __device__ __forceinline__ void collide_cell(const Geom& g, const Ptrs<T>& P, co
   if (SOLID) {
 #pragma unroll
     for (int q = 0; q < 27; ++q)
-      if ((mask >> OPP(q)) & 1u) f[q] += ld(P.aux_in + q * S + nbr(c, -CX(q), -CY(q), -CZ(q)));
+      if ((mask >> OPP(q)) & 1u) f[q] += ld(P.aux_in + rd_dir<SM>(q) * S + nbr(c, RS * CX(q), RS * CY(q), RS * CZ(q)));
   }
   const T rr = ld(P.mac + i0), rb = ld(P.mac + S + i0);
   const T F[3] = {ld(P.force + i0), ld(P.force + S + i0), ld(P.force + 2 * S + i0)};
@@ -690,7 +694,8 @@ __device__ __forceinline__ void collide_cell(const Geom& g, const Ptrs<T>& P, co
   const T r0n = SHIFT ? P.s_out[S_REST * S + i0] : T(0);
 #pragma unroll
   for (int q = 0; q < 27; ++q)
-    fout<SF>(P.f_out)[pop_index<SHIFT>(q, S, i0)] = Store<SF>::put(pop_encode<SHIFT>(q, f[q], r0n, ph.rest1));
+    fout<SF>(P.f_out)[pop_index<SHIFT>(wr_dir<SM>(q), S, SM == SM_ODD ? nbr(c, CX(q), CY(q), CZ(q)) : i0)] =
+        Store<SF>::put(pop_encode<SHIFT>(q, f[q], r0n, ph.rest1));
 }
 
 // ---- kernels of one domain ------------------------------------------------------------------
@@ -698,11 +703,11 @@ __device__ __forceinline__ void collide_cell(const Geom& g, const Ptrs<T>& P, co
 // in x, tiles in y, chunks of tz planes) of TX x TY blocks for the z-marching
 // passes; one thread per cell, one z plane per blockIdx.z, for the collision.
 
-template <typename T, typename SF, bool SOLID>
+template <typename T, typename SF, bool SOLID, int SM = SM_AB>
 __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !SOLID) ? 4 : 1)
     k_macro(Geom g, Ptrs<T> P, Phys<T> ph, int tz, int zb, int ze) {
   const int z0 = zb + blockIdx.z * tz;
-  macro_tile<T, SF, SOLID>(g, P, ph, z0, min(ze, z0 + tz), blockIdx.x, blockIdx.y);
+  macro_tile<T, SF, SOLID, SM>(g, P, ph, z0, min(ze, z0 + tz), blockIdx.x, blockIdx.y);
 }
 
 template <typename T, bool SOLID>
@@ -723,14 +728,14 @@ __global__ void __launch_bounds__(NT) k_div_sep(Geom g, Ptrs<T> P, int tz, int u
   div_sep_tile<T>(g, P, z0, min(ze, z0 + tz), use_Q, blockIdx.x, blockIdx.y);
 }
 
-template <typename T, typename SF, bool SOLID, bool UNIT>
+template <typename T, typename SF, bool SOLID, bool UNIT, int SM = SM_AB>
 __global__ void __launch_bounds__(128, 6) k_collide(Geom g, Ptrs<T> P, Phys<T> ph, int zb) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= g.nx || y >= g.ny) return;
   Cell c;
   make_cell_at(g, x, y, zb + blockIdx.z, c);
-  collide_cell<T, SF, SOLID, UNIT>(g, P, ph, c);
+  collide_cell<T, SF, SOLID, UNIT, SM>(g, P, ph, c);
 }
 
 // ---- kernels of a batch of domains -----------------------------------------------------------

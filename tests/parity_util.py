@@ -14,15 +14,16 @@ def rel_err(a, ref, floor=0.0):
     return float(np.abs(a - ref).max() / scale) if scale > 0 else float(np.abs(a - ref).max())
 
 
-def run_pair(params: dict, fields, steps, precision="f64", solid=None, oracle_steps=None):
-    """Advance the oracle and the GPU domain from the same fields; return both."""
+def run_pair(params: dict, fields, steps, precision="f64", solid=None, oracle_steps=None, streaming=0):
+    """Advance the oracle and the GPU domain from the same fields; return both.
+    `streaming` selects the GPU population layout (the oracle has one)."""
     import oracle
     from paper_2309_07801_gb300 import cg
     rr, rb, u = fields
     od = oracle.Domain(oracle.make_params(**params))
     od.init(rr, rb, u, solid)
     od.step(steps if oracle_steps is None else oracle_steps)
-    gd = cg.Domain(cg.make_params(precision=precision,
+    gd = cg.Domain(cg.make_params(precision=precision, streaming=streaming,
                                   solid_mask=1 if solid is not None else 0, **params))
     gd.init(rr, rb, u, solid)
     gd.step(steps)

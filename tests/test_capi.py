@@ -36,8 +36,8 @@ def test_every_declared_symbol_is_exported(cg):
 def test_params_struct_layout_matches_header(cg):
     # offsets follow the C declaration order; size includes the trailing ints
     p = cg.cg_params()
-    assert ctypes.sizeof(p) == 4 * 6 + 8 * 8 + 8 * 11 + 8 * 3 + 8 + 4 * 6 + 8 * 18
-    assert cg.cg_abi_version() == 2
+    assert ctypes.sizeof(p) == 4 * 6 + 8 * 8 + 8 * 11 + 8 * 3 + 8 + 4 * 6 + 8 * 18 + 4 * 2
+    assert cg.cg_abi_version() == 3
 
 
 def test_defaults_and_workspace(cg):
@@ -145,3 +145,28 @@ def test_d2q9_parameters_validated(cg):
         nz = kw.pop("nz", 1)
         with pytest.raises(cg.CGError):
             cg.cg_workspace_bytes(cg.make_params(16, 8, nz, **kw))
+
+
+@pytest.mark.parametrize("precision,walls", [("f64", False), ("f32", True), ("f16s", False)])
+def test_in_place_streaming_saves_one_population_copy(cg, precision, walls):
+    """CG_STREAM_IN_PLACE keeps one population buffer (and one wall buffer)."""
+    p = cg.make_params(40, 24, 16, precision=precision, bc=(0, 0, 1) if walls else (0, 0, 0))
+    two = cg.cg_workspace_bytes(p)
+    p.streaming = cg.CG_STREAM_IN_PLACE
+    one = cg.cg_workspace_bytes(p)
+    stride = (40 * 24 * 16 + 63) // 64 * 64
+    pop = {"f64": 8, "f32": 4, "f16s": 2}[precision]
+    saved = 27 * stride * pop + (27 * stride * 4 if walls else 0)
+    assert abs((two - one) - saved) <= 2 * 256, (two, one, saved)
+
+
+def test_in_place_streaming_validation(cg):
+    p = cg.make_params(16, 16, 1, lattice=cg.CG_D2Q9, streaming=cg.CG_STREAM_IN_PLACE)
+    with pytest.raises(cg.CGError) as e:
+        cg.cg_workspace_bytes(p)
+    assert e.value.code == -2 and "D3Q27" in str(e.value)
+    for bad in (("streaming", 2), ("streaming", -1), ("reserved0", 1)):
+        p = cg.make_params(8, 8, 8, **dict([bad]))
+        with pytest.raises(cg.CGError) as e:
+            cg.cg_workspace_bytes(p)
+        assert e.value.code == -1

@@ -235,15 +235,20 @@ int cg_destroy(cg_ctx *ctx);
 
 /* ---- batches: many domains advanced in shared launches -------------------
  * The paper has no counterpart: this is the library's way of running many
- * independent simulations (different sizes and parameters) at once.  A batch
- * step advances every member domain by one time step with four launches in
- * total: each pass runs over a work list that concatenates the tiles of all
- * members, with the arithmetic of cg_step() for every cell, so each member's
- * results are bitwise those of stepping it alone.  The four launches are
- * captured into CUDA graphs (per step parity) and replayed; the z depth of
- * the tiles is tuned online by timing three depths on the first steps after
- * the member set has changed by more than a factor two in cells (those steps
- * are ordinary steps: results do not depend on the depth).
+ * independent simulations (different sizes and parameters) at once.  The
+ * members form up to four contiguous groups of about equal cell counts; a
+ * batch step is four launches per group, each pass running over a work list
+ * that concatenates the tiles of the group's members, with the arithmetic of
+ * cg_step() for every cell.  A member's results are bitwise those of stepping
+ * it alone in FP64, and within the storage precision's rounding in FP32 and
+ * the 16-bit modes (the batched kernels are compiled separately and may fuse
+ * other products into FMAs); they never depend on the other members.  The
+ * launches are built into CUDA graphs (per step parity; eight steps per graph
+ * when enough are requested) in which the groups' passes run concurrently;
+ * the z depth of the tiles is tuned online by timing three depths on the
+ * first steps after the member set has changed by more than a factor two in
+ * cells (those steps are ordinary steps: results do not depend on the
+ * depth).
  *
  * Members must share the batch's precision and kernel variant (walls or none;
  * unit-rate Model D or not), else CG_ERR_UNSUPPORTED.  While a domain is a

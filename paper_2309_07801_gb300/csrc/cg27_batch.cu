@@ -2,12 +2,16 @@
 //
 // A batch holds up to max_domains initialised domains of one precision and
 // one kernel variant (walls or none; unit-rate Model D or the general
-// collision).  One batch step is four launches whatever the number of
-// members: each pass runs over a work list that concatenates the tiles of all
-// members (cg27_step.cuh, "kernels of a batch of domains").  The descriptor
-// table and the work lists live in the caller's batch workspace; the four
-// launches of a step are captured once per step parity into CUDA graphs and
-// replayed.  The z depth of the tiles is tuned online: the first steps after
+// collision).  One batch step is four launches per group of members, whatever
+// the number of members: each pass runs over a work list that concatenates the
+// tiles of the group's members (cg27_step.cuh, "kernels of a batch of domains").  The descriptor
+// table and the work lists live in the caller's batch workspace.  The members
+// form up to BATCH_GROUPS contiguous groups of about equal cell counts, and a
+// CUDA graph holds the four passes of every group as independent chains (the
+// passes of one group wait only for that group), so the issue-bound stencil
+// passes of one group overlap the bandwidth-bound population passes of another;
+// BATCH_CHAIN consecutive steps go into one graph, each group's step t+1 after
+// its step t.  Graphs are built per step parity and replayed.  The z depth of the tiles is tuned online: the first steps after
 // the member set has changed noticeably are timed for three depths and the
 // fastest is kept (the results of a cell do not depend on the depth, so the
 // tuning steps are ordinary steps of the simulation).
@@ -21,6 +25,8 @@ using namespace cg27;
 namespace {
 
 constexpr int TUNE_STEPS = 3;  // timed steps per candidate depth
+constexpr int BATCH_GROUPS = 4;  // member groups whose passes run concurrently
+constexpr int BATCH_CHAIN = 8;   // steps per graph when enough steps are requested
 
 size_t dom_bytes(int precision) {
   return precision == CG_F64 ? sizeof(Dom<double>) : sizeof(Dom<float>);
@@ -66,7 +72,11 @@ struct cg_batch {
   int tiles = 0, cell_blocks = 0;
   bool dirty = true;     // member set or depth changed since the table was written
   int64_t table_steps = 0;  // batch steps since the table was written (selects the parity)
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // member groups of the current table: members gdom[k] .. gdom[k+1]-1, tile
+  // items gitem[k] .. gitem[k+1]-1, collision blocks cs[gdom[k]] .. cs[gdom[k+1]]-1
+  std::vector<int> gdom, gitem, cs;
+  // graphs [one step | BATCH_CHAIN steps][parity of the first step]
+  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   bool use_graphs = true;
   // depth tuning
   int fixed_tz = 0;              // > 0: set by the caller, no tuning
@@ -77,8 +87,9 @@ struct cg_batch {
   int64_t steps = 0;
 
   ~cg_batch() {
-    for (auto& g : graph)
-      if (g) cudaGraphExecDestroy(g);
+    for (auto& row : graph)
+      for (auto& g : row)
+        if (g) cudaGraphExecDestroy(g);
     for (auto e : ev)
       if (e) cudaEventDestroy(e);
     for (cg_ctx* c : members) {
@@ -88,11 +99,12 @@ struct cg_batch {
   }
 
   void drop_graphs() {
-    for (auto& g : graph)
-      if (g) {
-        cudaGraphExecDestroy(g);
-        g = nullptr;
-      }
+    for (auto& row : graph)
+      for (auto& g : row)
+        if (g) {
+          cudaGraphExecDestroy(g);
+          g = nullptr;
+        }
   }
 };
 
@@ -140,7 +152,7 @@ int write_table(cg_batch* b) {
   if (count_items(b, tz) > b->L.max_items) return fail(CG_ERR_UNSUPPORTED, "batch tile table too small");
   b->tz = tz;
   std::vector<Dom<T>> doms(nd);
-  std::vector<int> cs(nd + 1);
+  std::vector<int> cs(nd + 1), istart(nd + 1);
   std::vector<int4> items;
   items.reserve((size_t)count_items(b, tz));
   cs[0] = 0;
@@ -157,6 +169,7 @@ int write_table(cg_batch* b) {
     D.tiles_y = (c->prm.ny + TY - 1) / TY;
     D.use_Q = c->prm.use_Q;
     const int chunks = (c->prm.nz + D.tz - 1) / D.tz;
+    istart[d] = (int)items.size();
     for (int bz = 0; bz < chunks; ++bz)
       for (int by = 0; by < D.tiles_y; ++by)
         for (int bx = 0; bx < D.tiles_x; ++bx) items.push_back(make_int4(d, bx, by, bz));
@@ -166,6 +179,21 @@ int write_table(cg_batch* b) {
   }
   b->tiles = (int)items.size();
   b->cell_blocks = cs[nd];
+  istart[nd] = b->tiles;
+  // contiguous member groups of about total / BATCH_GROUPS cells each
+  long long total = 0;
+  for (const cg_ctx* c : b->members) total += c->L.n;
+  b->gdom.assign(1, 0);
+  long long cum = 0;
+  for (int d = 0; d < nd; ++d) {
+    cum += b->members[d]->L.n;
+    const int k = (int)b->gdom.size();
+    if (k < BATCH_GROUPS && d + 1 < nd && cum * BATCH_GROUPS >= k * total) b->gdom.push_back(d + 1);
+  }
+  b->gdom.push_back(nd);
+  b->gitem.clear();
+  for (int g : b->gdom) b->gitem.push_back(istart[g]);
+  b->cs = cs;
   if (nd > 0) {
     CG_CUDA(cudaMemcpyAsync(b->ws + b->L.doms, doms.data(), nd * sizeof(Dom<T>), cudaMemcpyHostToDevice,
                             b->stream));
@@ -181,48 +209,101 @@ int write_table(cg_batch* b) {
   return CG_OK;
 }
 
+// launch shape and arguments of the four passes of member group k
+template <typename T>
+struct GroupPass {
+  const Dom<T>* doms;   // all members (the tile items name their domain)
+  const Dom<T>* cdoms;  // from the group's first member (the collision)
+  const int4* items;
+  const int* cs;
+  int ndom, block0;
+  dim3 tiles, blocks;
+};
+
+template <typename T>
+GroupPass<T> group_pass(const cg_batch* b, int k) {
+  GroupPass<T> g;
+  const int d0 = b->gdom[k], d1 = b->gdom[k + 1];
+  g.doms = reinterpret_cast<const Dom<T>*>(b->ws + b->L.doms);
+  g.cdoms = g.doms + d0;
+  g.items = reinterpret_cast<const int4*>(b->ws + b->L.items) + b->gitem[k];
+  g.cs = reinterpret_cast<const int*>(b->ws + b->L.cell_start) + d0;
+  g.ndom = d1 - d0;
+  g.block0 = b->cs[d0];
+  g.tiles = dim3((unsigned)(b->gitem[k + 1] - b->gitem[k]));
+  g.blocks = dim3((unsigned)(b->cs[d1] - b->cs[d0]));
+  return g;
+}
+
 template <typename T, typename SF, bool SOLID, bool UNIT>
 void launch_step(cg_batch* b, int par) {
-  const Dom<T>* doms = reinterpret_cast<const Dom<T>*>(b->ws + b->L.doms);
-  const int4* items = reinterpret_cast<const int4*>(b->ws + b->L.items);
-  const int* cs = reinterpret_cast<const int*>(b->ws + b->L.cell_start);
-  const int nd = (int)b->members.size();
   const dim3 blk(TX, TY, 1);
-  k_macro_batch<T, SF, SOLID><<<b->tiles, blk, 0, b->stream>>>(doms, items, par);
-  k_fields_batch<T, SOLID><<<b->tiles, blk, 0, b->stream>>>(doms, items, par);
-  k_div_batch<T><<<b->tiles, blk, 0, b->stream>>>(doms, items, par);
-  k_collide_batch<T, SF, SOLID, UNIT><<<b->cell_blocks, 128, 0, b->stream>>>(doms, cs, nd, par);
+  for (int k = 0; k + 1 < (int)b->gdom.size(); ++k) {
+    const GroupPass<T> g = group_pass<T>(b, k);
+    k_macro_batch<T, SF, SOLID><<<g.tiles, blk, 0, b->stream>>>(g.doms, g.items, par);
+    k_fields_batch<T, SOLID><<<g.tiles, blk, 0, b->stream>>>(g.doms, g.items, par);
+    k_div_batch<T><<<g.tiles, blk, 0, b->stream>>>(g.doms, g.items, par);
+    k_collide_batch<T, SF, SOLID, UNIT><<<g.blocks, 128, 0, b->stream>>>(g.cdoms, g.cs, g.ndom, par, g.block0);
+  }
+}
+
+// nsteps steps from parity par0: per group a chain of its four passes per step
+template <typename T, typename SF, bool SOLID, bool UNIT>
+cudaGraphExec_t build_batch_graph(const cg_batch* b, int par0, int nsteps) {
+  cudaGraph_t gph;
+  if (cudaGraphCreate(&gph, 0) != cudaSuccess) return nullptr;
+  bool ok = true;
+  const dim3 blk(TX, TY, 1), cblk(128, 1, 1);
+  const int ng = (int)b->gdom.size() - 1;
+  std::vector<cudaGraphNode_t> last(ng, nullptr);
+  void* fn[4] = {(void*)k_macro_batch<T, SF, SOLID>, (void*)k_fields_batch<T, SOLID>, (void*)k_div_batch<T>,
+                 (void*)k_collide_batch<T, SF, SOLID, UNIT>};
+  for (int s = 0; s < nsteps && ok; ++s) {
+    int par = (par0 + s) & 1;
+    for (int k = 0; k < ng && ok; ++k) {
+      GroupPass<T> g = group_pass<T>(b, k);
+      void* a_tile[] = {(void*)&g.doms, (void*)&g.items, (void*)&par};
+      void* a_coll[] = {(void*)&g.cdoms, (void*)&g.cs, (void*)&g.ndom, (void*)&par, (void*)&g.block0};
+      for (int p = 0; p < 4 && ok; ++p) {
+        cudaKernelNodeParams kp = {};
+        kp.func = fn[p];
+        kp.gridDim = p < 3 ? g.tiles : g.blocks;
+        kp.blockDim = p < 3 ? blk : cblk;
+        kp.kernelParams = p < 3 ? a_tile : a_coll;
+        cudaGraphNode_t node = nullptr;
+        if (cudaGraphAddKernelNode(&node, gph, last[k] ? &last[k] : nullptr, last[k] ? 1 : 0, &kp) != cudaSuccess)
+          ok = false;
+        last[k] = node;
+      }
+    }
+  }
+  cudaGraphExec_t ex = nullptr;
+  if (!ok || cudaGraphInstantiate(&ex, gph, 0) != cudaSuccess) ex = nullptr;
+  cudaGraphDestroy(gph);
+  return ex;
 }
 
 template <typename T, typename SF, bool SOLID, bool UNIT>
 int run_steps(cg_batch* b, int64_t n) {
-  for (int64_t s = 0; s < n; ++s) {
+  for (int64_t s = 0; s < n;) {
     const int par = (int)(b->table_steps & 1);
-    if (b->use_graphs) {
-      if (!b->graph[par]) {
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-          launch_step<T, SF, SOLID, UNIT>(b, par);
-          e = cudaStreamEndCapture(b->stream, &g);
-        }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph[par], g, 0);
-        if (g) cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-          // capture is not available on this stream: plain launches from now on
-          (void)cudaGetLastError();
-          b->graph[par] = nullptr;
-          b->use_graphs = false;
-        }
+    const int k = (n - s >= BATCH_CHAIN) ? 1 : 0;
+    const int m = k ? BATCH_CHAIN : 1;
+    if (b->use_graphs && !b->graph[k][par]) {
+      b->graph[k][par] = build_batch_graph<T, SF, SOLID, UNIT>(b, par, m);
+      if (!b->graph[k][par]) {
+        (void)cudaGetLastError();
+        b->use_graphs = false;  // graphs unavailable here: plain launches from now on
       }
     }
     if (b->use_graphs)
-      CG_CUDA(cudaGraphLaunch(b->graph[par], b->stream));
+      CG_CUDA(cudaGraphLaunch(b->graph[k][par], b->stream));
     else
-      launch_step<T, SF, SOLID, UNIT>(b, par);
-    ++b->table_steps;
-    ++b->steps;
-    for (cg_ctx* c : b->members) ++c->steps;
+      for (int i = 0; i < m; ++i) launch_step<T, SF, SOLID, UNIT>(b, (par + i) & 1);
+    b->table_steps += m;
+    b->steps += m;
+    for (cg_ctx* c : b->members) c->steps += m;
+    s += m;
   }
   CG_CUDA(cudaGetLastError());
   return CG_OK;

@@ -797,11 +797,15 @@ __global__ void __launch_bounds__(NT)
 
 template <typename T, typename SF, bool SOLID, bool UNIT>
 __global__ void __launch_bounds__(128, 6)
-    k_collide_batch(const Dom<T>* __restrict__ doms, const int* __restrict__ start, int ndom, int par) {
-  const int d = find_domain(start, ndom, blockIdx.x);
+    k_collide_batch(const Dom<T>* __restrict__ doms, const int* __restrict__ start, int ndom, int par,
+                    int block0) {
+  // doms and start point at the first domain of a group of members; block0 is
+  // that domain's first block in the batch-wide numbering of start
+  const int blk = (int)blockIdx.x + block0;
+  const int d = find_domain(start, ndom, blk);
   const Dom<T>& D = doms[d];
   // domains hold fewer than 2^31 cells, so 32-bit unsigned index arithmetic is exact
-  const unsigned i = (unsigned)(blockIdx.x - __ldg(start + d)) * 128u + threadIdx.x;
+  const unsigned i = (unsigned)(blk - __ldg(start + d)) * 128u + threadIdx.x;
   const unsigned nxy = (unsigned)D.g.nxy, nx = (unsigned)D.g.nx;
   if (i >= nxy * (unsigned)D.g.nz) return;
   const unsigned z = i / nxy, r = i - z * nxy, y = r / nx;

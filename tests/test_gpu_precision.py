@@ -13,6 +13,8 @@ these exact runs; they state the accuracy of each storage mode:
   200 steps (vs oracle)                 |du|              1e-6     2e-4     2e-3
   Laplace 32^3, 2000 steps (vs FP64)    dp relative       -        2e-4     2e-3
   head-on collision 64^3, 1500 steps    mass drift        -        5e-5     5e-5
+  translating droplet 64^3, 1000 steps, centroid vs FP32 -  1e-2     5e-1
+  read back every 250 steps             mass drift        -        1e-4     5e-3
 """
 import numpy as np
 import pytest
@@ -92,3 +94,17 @@ def test_head_on_collision_mass_and_interface(prec):
     mismatch = (np.sign(phi) != np.sign(phi_ref)).sum() / iface.sum()
     assert mismatch < 0.1, mismatch
 
+
+
+@pytest.mark.parametrize("prec,cen_tol,mass_tol", [("f16s", 0.01, 1e-4), ("bf16s", 0.5, 5e-3)])
+def test_translating_droplet_64_with_samples(prec, cen_tol, mass_tol):
+    """The ratio-10 translating droplet (64^3, Mach about 0.4 in the heavy
+    phase) for 1000 steps, read back every 250 steps as the studies do: no
+    non-finite density, the centroid within cen_tol cells of the FP32 run and
+    the per-colour mass drift below mass_tol."""
+    from paper_2309_07801_gb300 import studies
+    ref = studies.translating(64, 1000, 250, "f32")["samples"]
+    got = studies.translating(64, 1000, 250, prec)["samples"]
+    assert len(got) == len(ref) == 5 and all(s["nonfinite"] == 0 for s in got)
+    assert np.max(np.abs(np.array(got[-1]["centroid"]) - np.array(ref[-1]["centroid"]))) < cen_tol
+    assert max(got[-1]["mass_drift"]) < mass_tol

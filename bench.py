@@ -97,9 +97,9 @@ def recorded_traffic(kernel, cells):
     return None
 
 
-def step_slabs(nz, planes=24):
+def step_slabs(nz, planes=16):
     """Kernels per pass in one step: the library runs a domain with at least two
-    z slabs of 24 planes as a graph of per-slab kernels (cg27_capi.cu)."""
+    z slabs of 16 planes as a graph of per-slab kernels (cg27_capi.cu)."""
     return (nz + planes - 1) // planes if nz >= 2 * planes else 1
 
 

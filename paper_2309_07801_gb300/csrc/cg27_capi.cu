@@ -149,9 +149,11 @@ dim3 grid_of(const cg_params& p, dim3 b) {
 }
 
 // z slabs of the step graphs: SLAB_PLANES planes in chunks of SLAB_TZ per tile
-// (24 and 8 measured best at 128^3 on GB300 among 14-43 and 7-16)
-constexpr int SLAB_PLANES = 24, SLAB_TZ = 8;
-// steps chained in one slab graph (8: +6 % over one step per graph at 128^3)
+// (16 and 8 measured best at 128^3 on GB300, with eight-step chains, among
+// 16/24/32/48 planes and 4/8/12/16 per tile)
+constexpr int SLAB_PLANES = 16, SLAB_TZ = 8;
+// steps chained in one slab graph (8: +6 % over one step per graph at 128^3,
+// 16 gains 0.3 % more)
 constexpr int GRAPH_STEPS = 8;
 
 // the macroscopic pass and the collision of a step of stream mode sm

@@ -636,16 +636,36 @@ __device__ __forceinline__ void collide_cell(const Geom& g, const Ptrs<T>& P, co
     // by the cell's wall rule (bounce-back, specular, or moving)
     T uw[3];
     const int flip = wall_rule(g, ph, c, uw);
-    for (int q = 0; q < 27; ++q) {
-      const int src = nbr(c, -CX(q), -CY(q), -CZ(q));
-      T fr, fb, ft;
-      pull_colour<T, SF, SOLID>(P, S, q, src, pull_index(SM, q, S, c), mask, fr, fb, ft);
-      const bool fluid_src = !((mask >> OPP(q)) & 1u);
-      const int out = wall_emit(q, flip, uw, fluid_src ? ld(P.mac + src) : T(0),
-                                fluid_src ? ld(P.mac + S + src) : T(0), fr, fb);
-      const long long o = emit_index(SM, out, S, c);
-      fout<SF>(P.f_out)[o] = Store<SF>::put(fr);
-      P.aux_out[o] = fb;
+    if constexpr (SM == SM_AB) {
+      for (int q = 0; q < 27; ++q) {
+        const int src = nbr(c, -CX(q), -CY(q), -CZ(q));
+        T fr, fb, ft;
+        pull_colour<T, SF, SOLID>(P, S, q, src, pull_index(SM, q, S, c), mask, fr, fb, ft);
+        const bool fluid_src = !((mask >> OPP(q)) & 1u);
+        const int out = wall_emit(q, flip, uw, fluid_src ? ld(P.mac + src) : T(0),
+                                  fluid_src ? ld(P.mac + S + src) : T(0), fr, fb);
+        const long long o = emit_index(SM, out, S, c);
+        fout<SF>(P.f_out)[o] = Store<SF>::put(fr);
+        P.aux_out[o] = fb;
+      }
+    } else {
+      // in place, the slots this cell writes are the ones it reads: read all
+      // 27 first (a slip wall sends direction q into another direction's slot)
+      T fr[27], fb[27];
+      int out[27];
+      for (int q = 0; q < 27; ++q) {
+        const int src = nbr(c, -CX(q), -CY(q), -CZ(q));
+        T ft;
+        pull_colour<T, SF, SOLID>(P, S, q, src, pull_index(SM, q, S, c), mask, fr[q], fb[q], ft);
+        const bool fluid_src = !((mask >> OPP(q)) & 1u);
+        out[q] = wall_emit(q, flip, uw, fluid_src ? ld(P.mac + src) : T(0),
+                           fluid_src ? ld(P.mac + S + src) : T(0), fr[q], fb[q]);
+      }
+      for (int q = 0; q < 27; ++q) {
+        const long long o = emit_index(SM, out[q], S, c);
+        fout<SF>(P.f_out)[o] = Store<SF>::put(fr[q]);
+        P.aux_out[o] = fb[q];
+      }
     }
     return;
   }

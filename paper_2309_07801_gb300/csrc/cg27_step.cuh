@@ -712,9 +712,21 @@ __device__ __forceinline__ void collide_cell(const Geom& g, const Ptrs<T>& P, co
   collide_cm<T, UNIT>(f, rho, p, u[0], u[1], u[2], F, Q, om1, ph);
   // the rest-direction shift is the value the field pass stored for this cell
   const T r0n = SHIFT ? P.s_out[S_REST * S + i0] : T(0);
+  // In place, the slot written for direction q is the slot read for opp q:
+  // opaque copies of the stride and the cell offsets make the compiler form
+  // the store addresses afresh instead of keeping 27 load addresses live
+  // across the collision (which spills at this register budget).
+  long long Sw = S;
+  Cell cw = c;
+  if constexpr (SM != SM_AB) {
+    asm volatile("" : "+l"(Sw));
+    asm volatile("" : "+r"(cw.idx));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) asm volatile("" : "+r"(cw.xs[k]), "+r"(cw.ys[k]), "+r"(cw.zs[k]));
+  }
 #pragma unroll
   for (int q = 0; q < 27; ++q)
-    fout<SF>(P.f_out)[pop_index<SHIFT>(wr_dir<SM>(q), S, SM == SM_ODD ? nbr(c, CX(q), CY(q), CZ(q)) : i0)] =
+    fout<SF>(P.f_out)[pop_index<SHIFT>(wr_dir<SM>(q), Sw, SM == SM_ODD ? nbr(cw, CX(q), CY(q), CZ(q)) : cw.idx)] =
         Store<SF>::put(pop_encode<SHIFT>(q, f[q], r0n, ph.rest1));
 }
 

@@ -11,7 +11,9 @@ domains only, so there is no collective on the data path; scaling is weak).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-The line also carries a serving measurement ("serving"): 256 independent static
+The line also carries the same workload in the 16-bit storage modes and with
+in-place streaming ("variants": MLUPS and workspace bytes of each), and a
+serving measurement ("serving"): 256 independent static
 or oscillating droplet runs (edges 32..128, ratio 1..10, 500..5000 steps) with
 Poisson arrivals, admitted by free device memory and advanced together in
 shared launches (continuous batching); it reports p50/p99 time to result,
@@ -54,6 +56,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the other storage modes and in-place streaming")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-rate", type=float, default=3.8,
                     help="Poisson arrivals per second (about 0.8 of the batched capacity)")
@@ -366,6 +370,10 @@ def run_ours(args, dist):
             "roofline": roofline, "step_roofline_432B": step_roofline,
             "e2e": e2e, "gpu_launches": len(cg.PASS_NAMES) * K * step_slabs(wl.nz), "clocks": clk,
             "mass": list(map(float, mass)), "nonfinite": nonfinite}
+    if not args.no_variants:
+        line["variants"] = variants(wl, (rr, rb, u), min(K, 800))
+        line["variants"]["f32_two_buffers"] = {"MLUPS": value / dist.world,
+                                              "workspace_bytes": cg.cg_workspace_bytes(params)}
     if not args.no_serve:
         line["serving"] = serving(args)
     if not args.no_cpu_baseline and dist.world == 1:
@@ -373,6 +381,35 @@ def run_ours(args, dist):
     elif not args.no_cpu_baseline:
         line["cpu_baseline"] = None
     print(json.dumps(line), flush=True)
+
+
+def variants(wl, fields, steps):
+    """The same workload in the other storage modes and with in-place
+    streaming: MLUPS (CUDA events around `steps` steps, best of two) and the
+    workspace each needs.  Accuracy of the 16-bit modes: tests/test_gpu_precision.py."""
+    import torch
+    from paper_2309_07801_gb300 import cg
+    out = {}
+    for prec, streaming in (("f32", 1), ("f16s", 0), ("f16s", 1), ("bf16s", 0), ("bf16s", 1)):
+        p = cg.make_params(precision=prec, streaming=streaming, **wl.params())
+        d = cg.Domain(p)
+        d.init(*fields)
+        d.step(16)
+        s = d.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = float("inf")
+        for _ in range(2):
+            e0.record(s)
+            cg.cg_step(d.h, steps)
+            e1.record(s)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        mass, nonfinite = d.mass()
+        d.close()
+        out["%s_%s" % (prec, "in_place" if streaming else "two_buffers")] = {
+            "MLUPS": wl.cells * steps / (best * 1e-3) / 1e6, "workspace_bytes": cg.cg_workspace_bytes(p),
+            "nonfinite": nonfinite}
+    return out
 
 
 def _serve(mode, reqs):

@@ -236,7 +236,7 @@ int cg_destroy(cg_ctx *ctx);
 /* ---- batches: many domains advanced in shared launches -------------------
  * The paper has no counterpart: this is the library's way of running many
  * independent simulations (different sizes and parameters) at once.  The
- * members form up to four contiguous groups of about equal cell counts; a
+ * members form up to sixteen contiguous groups of about equal cell counts; a
  * batch step is four launches per group, each pass running over a work list
  * that concatenates the tiles of the group's members, with the arithmetic of
  * cg_step() for every cell.  A member's results are bitwise those of stepping
@@ -290,11 +290,21 @@ int cg_batch_step(cg_batch *batch, int64_t nsteps);
 int cg_batch_sync(cg_batch *batch);
 
 /* Fix the z depth of the tiles (planes per tile, > 0), or 0 to tune it
- * online again. */
+ * online again (together with the grid form unless that is fixed). */
 int cg_batch_set_depth(cg_batch *batch, int32_t tz);
 
 /* Current depth (0 before the first step) and whether tuning is under way. */
 int cg_batch_depth(cg_batch *batch, int32_t *tz, int32_t *tuning);
+
+/* Grid form of the batch kernels: 0 one block per work item (tile or 128
+ * cells), 1 persistent (each group's kernels launch its share of the blocks the
+ * GPU holds at once, which walk the work list), or -1 to let the online tuner
+ * choose (the default; it times both forms at each candidate depth).  Results
+ * do not depend on the form.  CG_ERR_INVALID_ARG for other values. */
+int cg_batch_set_persistent(cg_batch *batch, int32_t mode);
+
+/* The grid form in use (0 or 1). */
+int cg_batch_persistent(cg_batch *batch, int32_t *mode);
 
 /* Release the batch (waits for its stream; members become free domains). */
 int cg_batch_destroy(cg_batch *batch);

@@ -81,6 +81,8 @@ SIGNATURES = {
     "cg_batch_sync": (ctypes.c_int, [_VP]),
     "cg_batch_set_depth": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "cg_batch_depth": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "cg_batch_set_persistent": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "cg_batch_persistent": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32)]),
     "cg_batch_destroy": (ctypes.c_int, [_VP])
 }
 
@@ -359,6 +361,16 @@ def cg_batch_depth(b):
     return tz.value, bool(tuning.value)
 
 
+def cg_batch_set_persistent(b, mode: int):
+    _check(lib().cg_batch_set_persistent(b, int(mode)))
+
+
+def cg_batch_persistent(b) -> int:
+    m = ctypes.c_int32(0)
+    _check(lib().cg_batch_persistent(b, ctypes.byref(m)))
+    return m.value
+
+
 def cg_batch_destroy(b):
     _check(lib().cg_batch_destroy(b))
 
@@ -397,6 +409,13 @@ class Batch:
     @property
     def depth(self):
         return cg_batch_depth(self.h)
+
+    def set_persistent(self, mode: int):
+        cg_batch_set_persistent(self.h, mode)
+
+    @property
+    def persistent(self) -> int:
+        return cg_batch_persistent(self.h)
 
     def __len__(self):
         return cg_batch_size(self.h)

@@ -25,7 +25,7 @@ using namespace cg27;
 namespace {
 
 constexpr int TUNE_STEPS = 3;  // timed steps per candidate depth
-constexpr int BATCH_GROUPS = 4;  // member groups whose passes run concurrently
+constexpr int BATCH_GROUPS = 16;  // member groups whose passes run concurrently (4..32 within 1 %)
 constexpr int BATCH_CHAIN = 8;   // steps per graph when enough steps are requested
 
 size_t dom_bytes(int precision) {
@@ -78,11 +78,17 @@ struct cg_batch {
   // graphs [one step | BATCH_CHAIN steps][parity of the first step]
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   bool use_graphs = true;
-  // depth tuning
-  int fixed_tz = 0;              // > 0: set by the caller, no tuning
+  // launch schedule: tile depth and grid form (0: one block per work item,
+  // 1: persistent, a grid of the blocks the GPU holds at once walking the list)
+  int persist = 0;
+  int resident[4] = {0, 0, 0, 0};  // blocks per SM of the four batch kernels
+  int sms = 0;
+  // tuning of the schedule
+  int fixed_tz = 0;              // > 0: set by the caller, not tuned
+  int fixed_persist = -1;        // >= 0: set by the caller, not tuned
   long long tuned_cells = 0;     // cell count the current choice was tuned for
-  std::vector<int> cand;         // candidates still to time
-  std::vector<std::pair<double, int>> timed;  // (ms per cell-update, depth)
+  std::vector<std::pair<int, int>> cand;  // (depth, grid form) still to time
+  std::vector<std::pair<double, std::pair<int, int>>> timed;  // (ms per step, candidate)
   cudaEvent_t ev[2] = {nullptr, nullptr};
   int64_t steps = 0;
 
@@ -217,8 +223,18 @@ struct GroupPass {
   const int4* items;
   const int* cs;
   int ndom, block0;
-  dim3 tiles, blocks;
+  int ntiles, nblocks;  // work items of the tile passes and of the collision
+  dim3 grid[4];         // grids of macro, fields, div, collide
 };
+
+// grid of a pass over `items` work items in one of ngroups concurrent groups:
+// one block per item, or the group's share of the blocks the GPU holds at once
+unsigned pass_grid(const cg_batch* b, int items, int kernel) {
+  if (!b->persist) return (unsigned)items;
+  const int ng = (int)b->gdom.size() - 1;
+  const long long share = std::max(1LL, (long long)b->sms * std::max(1, b->resident[kernel]) / std::max(1, ng));
+  return (unsigned)std::min<long long>(items, share);
+}
 
 template <typename T>
 GroupPass<T> group_pass(const cg_batch* b, int k) {
@@ -230,8 +246,9 @@ GroupPass<T> group_pass(const cg_batch* b, int k) {
   g.cs = reinterpret_cast<const int*>(b->ws + b->L.cell_start) + d0;
   g.ndom = d1 - d0;
   g.block0 = b->cs[d0];
-  g.tiles = dim3((unsigned)(b->gitem[k + 1] - b->gitem[k]));
-  g.blocks = dim3((unsigned)(b->cs[d1] - b->cs[d0]));
+  g.ntiles = b->gitem[k + 1] - b->gitem[k];
+  g.nblocks = b->cs[d1] - b->cs[d0];
+  for (int p = 0; p < 4; ++p) g.grid[p] = dim3(pass_grid(b, p < 3 ? g.ntiles : g.nblocks, p));
   return g;
 }
 
@@ -240,10 +257,11 @@ void launch_step(cg_batch* b, int par) {
   const dim3 blk(TX, TY, 1);
   for (int k = 0; k + 1 < (int)b->gdom.size(); ++k) {
     const GroupPass<T> g = group_pass<T>(b, k);
-    k_macro_batch<T, SF, SOLID><<<g.tiles, blk, 0, b->stream>>>(g.doms, g.items, par);
-    k_fields_batch<T, SOLID><<<g.tiles, blk, 0, b->stream>>>(g.doms, g.items, par);
-    k_div_batch<T><<<g.tiles, blk, 0, b->stream>>>(g.doms, g.items, par);
-    k_collide_batch<T, SF, SOLID, UNIT><<<g.blocks, 128, 0, b->stream>>>(g.cdoms, g.cs, g.ndom, par, g.block0);
+    k_macro_batch<T, SF, SOLID><<<g.grid[0], blk, 0, b->stream>>>(g.doms, g.items, g.ntiles, par);
+    k_fields_batch<T, SOLID><<<g.grid[1], blk, 0, b->stream>>>(g.doms, g.items, g.ntiles, par);
+    k_div_batch<T><<<g.grid[2], blk, 0, b->stream>>>(g.doms, g.items, g.ntiles, par);
+    k_collide_batch<T, SF, SOLID, UNIT><<<g.grid[3], 128, 0, b->stream>>>(g.cdoms, g.cs, g.ndom, par, g.block0,
+                                                                         g.nblocks);
   }
 }
 
@@ -262,12 +280,13 @@ cudaGraphExec_t build_batch_graph(const cg_batch* b, int par0, int nsteps) {
     int par = (par0 + s) & 1;
     for (int k = 0; k < ng && ok; ++k) {
       GroupPass<T> g = group_pass<T>(b, k);
-      void* a_tile[] = {(void*)&g.doms, (void*)&g.items, (void*)&par};
-      void* a_coll[] = {(void*)&g.cdoms, (void*)&g.cs, (void*)&g.ndom, (void*)&par, (void*)&g.block0};
+      void* a_tile[] = {(void*)&g.doms, (void*)&g.items, (void*)&g.ntiles, (void*)&par};
+      void* a_coll[] = {(void*)&g.cdoms, (void*)&g.cs, (void*)&g.ndom, (void*)&par, (void*)&g.block0,
+                        (void*)&g.nblocks};
       for (int p = 0; p < 4 && ok; ++p) {
         cudaKernelNodeParams kp = {};
         kp.func = fn[p];
-        kp.gridDim = p < 3 ? g.tiles : g.blocks;
+        kp.gridDim = g.grid[p];
         kp.blockDim = p < 3 ? blk : cblk;
         kp.kernelParams = p < 3 ? a_tile : a_coll;
         cudaGraphNode_t node = nullptr;
@@ -285,6 +304,16 @@ cudaGraphExec_t build_batch_graph(const cg_batch* b, int par0, int nsteps) {
 
 template <typename T, typename SF, bool SOLID, bool UNIT>
 int run_steps(cg_batch* b, int64_t n) {
+  if (b->resident[0] == 0) {
+    // blocks per SM of the four kernels of this variant (the persistent grids)
+    int dev = 0;
+    CG_CUDA(cudaGetDevice(&dev));
+    CG_CUDA(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev));
+    const void* fn[4] = {(const void*)k_macro_batch<T, SF, SOLID>, (const void*)k_fields_batch<T, SOLID>,
+                         (const void*)k_div_batch<T>, (const void*)k_collide_batch<T, SF, SOLID, UNIT>};
+    for (int p = 0; p < 4; ++p)
+      CG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->resident[p], fn[p], p < 3 ? NT : 128, 0));
+  }
   for (int64_t s = 0; s < n;) {
     const int par = (int)(b->table_steps & 1);
     const int k = (n - s >= BATCH_CHAIN) ? 1 : 0;
@@ -333,15 +362,32 @@ int write_table_any(cg_batch* b) {
   return b->precision == CG_F64 ? write_table<double>(b) : write_table<float>(b);
 }
 
-// start tuning when the member set has changed by more than a factor two in cells
+// Start tuning when the member set has changed by more than a factor two in
+// cells: the candidates are three depths (the heuristic h, h/2, 2h) times the
+// two grid forms, less what the caller has fixed.
 void maybe_retune(cg_batch* b) {
-  if (b->fixed_tz > 0 || b->members.empty()) return;
+  if (b->members.empty()) return;
   const long long n = total_cells(b);
   if (b->tuned_cells > 0 && n <= 2 * b->tuned_cells && 2 * n >= b->tuned_cells) return;
-  const int h = heuristic_tz(b), mz = max_nz(b);
+  std::vector<int> depths, forms;
+  if (b->fixed_tz > 0) {
+    depths.push_back(b->fixed_tz);
+  } else {
+    const int h = heuristic_tz(b), mz = max_nz(b);
+    for (int t : {h, std::max(1, h / 2), std::min(mz, 2 * h)})
+      if (std::find(depths.begin(), depths.end(), t) == depths.end()) depths.push_back(t);
+  }
+  if (b->fixed_persist >= 0) forms.push_back(b->fixed_persist);
+  else forms = {0, 1};
   b->cand.clear();
-  for (int t : {h, std::max(1, h / 2), std::min(mz, 2 * h)})
-    if (std::find(b->cand.begin(), b->cand.end(), t) == b->cand.end()) b->cand.push_back(t);
+  for (int t : depths)
+    for (int f : forms) b->cand.push_back({t, f});
+  if (b->cand.size() == 1) {  // nothing left to choose
+    b->tz = b->cand[0].first;
+    b->persist = b->cand[0].second;
+    b->cand.clear();
+    b->dirty = true;
+  }
   b->timed.clear();
   b->tuned_cells = n;
 }
@@ -422,6 +468,7 @@ int cg_batch_remove(cg_batch* b, cg_ctx* c) {
   if (b->members.empty()) {
     b->solid = b->unit = -1;
     b->tuned_cells = 0;
+    b->resident[0] = 0;  // the next member may bring another kernel variant
   } else {
     maybe_retune(b);
   }
@@ -444,9 +491,29 @@ int cg_batch_set_depth(cg_batch* b, int32_t tz) {
   if (tz > 0) {
     b->tz = tz;
     b->dirty = true;
-  } else {
-    maybe_retune(b);
   }
+  maybe_retune(b);
+  return CG_OK;
+}
+
+int cg_batch_set_persistent(cg_batch* b, int32_t mode) {
+  if (!b) return fail(CG_ERR_INVALID_ARG, "batch is NULL");
+  if (mode < -1 || mode > 1) return fail(CG_ERR_INVALID_ARG, "mode must be -1 (tuned), 0 or 1");
+  b->fixed_persist = mode;
+  b->tuned_cells = 0;
+  b->cand.clear();
+  b->timed.clear();
+  if (mode >= 0) {
+    b->persist = mode;
+    b->dirty = true;
+  }
+  maybe_retune(b);
+  return CG_OK;
+}
+
+int cg_batch_persistent(cg_batch* b, int32_t* mode) {
+  if (!b || !mode) return fail(CG_ERR_INVALID_ARG, "NULL argument");
+  *mode = b->persist;
   return CG_OK;
 }
 
@@ -466,13 +533,18 @@ int cg_batch_step(cg_batch* b, int64_t nsteps) {
     b->tz = b->fixed_tz;
     b->dirty = true;
   }
+  if (b->fixed_persist >= 0 && b->persist != b->fixed_persist) {
+    b->persist = b->fixed_persist;
+    b->dirty = true;
+  }
   if (b->tz == 0) b->tz = heuristic_tz(b);
-  // tuning: time TUNE_STEPS steps per candidate depth (one untimed step first,
-  // for the table write and the graph capture)
+  // tuning: time TUNE_STEPS steps per candidate schedule (one untimed step
+  // first, for the table write and the graph build)
   while (!b->cand.empty() && nsteps >= TUNE_STEPS + 1) {
-    const int t = b->cand.back();
+    const std::pair<int, int> t = b->cand.back();
     b->cand.pop_back();
-    b->tz = t;
+    b->tz = t.first;
+    b->persist = t.second;
     if ((rc = write_table_any(b))) return rc;
     if ((rc = run(b, 1))) return rc;
     CG_CUDA(cudaEventRecord(b->ev[0], b->stream));
@@ -484,7 +556,9 @@ int cg_batch_step(cg_batch* b, int64_t nsteps) {
     b->timed.push_back({ms / TUNE_STEPS, t});
     nsteps -= TUNE_STEPS + 1;
     if (b->cand.empty()) {
-      b->tz = std::min_element(b->timed.begin(), b->timed.end())->second;
+      const std::pair<int, int> best = std::min_element(b->timed.begin(), b->timed.end())->second;
+      b->tz = best.first;
+      b->persist = best.second;
       b->dirty = true;
     }
   }

@@ -771,12 +771,15 @@ __global__ void __launch_bounds__(128, 6) k_collide(Geom g, Ptrs<T> P, Phys<T> p
 }
 
 // ---- kernels of a batch of domains -----------------------------------------------------------
-// Every pass of every member domain is one launch over a work list: block b of
-// a z-marching pass reads its item (domain, tile x, tile y, z chunk) from a
-// table written on the host, so a block starts from one 16-byte load; block b
-// of the collision covers cells 128 (b - cell_start[d]) ... + 127 of the
-// domain d with cell_start[d] <= b < cell_start[d + 1], in storage order.  The
-// arithmetic of each cell is that of the single-domain kernels.
+// Every pass of every member domain is one launch over a work list: work item
+// i of a z-marching pass (domain, tile x, tile y, z chunk) comes from a table
+// written on the host, so a tile starts from one 16-byte load; collision item
+// b covers cells 128 (b - cell_start[d]) ... + 127 of the domain d with
+// cell_start[d] <= b < cell_start[d + 1], in storage order.  A block takes
+// items blockIdx.x, blockIdx.x + gridDim.x, ...: with one block per item this
+// is the plain form, with a grid of the resident blocks of the GPU it is a
+// persistent kernel that walks the list.  The arithmetic of each cell is that
+// of the single-domain kernels, whatever the grid.
 
 template <typename T>
 struct Dom {
@@ -797,53 +800,66 @@ __device__ __forceinline__ int find_domain(const int* __restrict__ start, int nd
   return lo;
 }
 
-// one z-marching tile of a batch: domain, tile x, tile y, z chunk
-__device__ __forceinline__ int4 tile_item(const int4* __restrict__ items) { return __ldg(items + blockIdx.x); }
-
+// Tiles of a z-marching batch pass: item i = (domain, tile x, tile y, z chunk).
+// A block that takes several tiles waits at a barrier before each further one,
+// so the next tile's shared-memory prologue follows the last reads of the
+// previous tile.
 template <typename T, typename SF, bool SOLID>
 __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !SOLID) ? 4 : 1)
-    k_macro_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int par) {
-  const int4 t = tile_item(items);
-  const Dom<T>& D = doms[t.x];
-  macro_tile<T, SF, SOLID>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
+    k_macro_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int nitems, int par) {
+  for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+    if (i != (int)blockIdx.x) __syncthreads();
+    const int4 t = __ldg(items + i);
+    const Dom<T>& D = doms[t.x];
+    macro_tile<T, SF, SOLID>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
+  }
 }
 
 template <typename T, bool SOLID>
 __global__ void __launch_bounds__(NT)
-    k_fields_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int par) {
-  const int4 t = tile_item(items);
-  const Dom<T>& D = doms[t.x];
-  if constexpr (!SOLID && sizeof(T) == 4)
-    fields_sep_tile<T>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
-  else
-    fields_tile<T, SOLID>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
+    k_fields_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int nitems, int par) {
+  for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+    if (i != (int)blockIdx.x) __syncthreads();
+    const int4 t = __ldg(items + i);
+    const Dom<T>& D = doms[t.x];
+    if constexpr (!SOLID && sizeof(T) == 4)
+      fields_sep_tile<T>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
+    else
+      fields_tile<T, SOLID>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
+  }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(NT)
-    k_div_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int par) {
-  const int4 t = tile_item(items);
-  const Dom<T>& D = doms[t.x];
-  div_sep_tile<T>(D.g, D.P[par], t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), D.use_Q, t.y, t.z);
+    k_div_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int nitems, int par) {
+  for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+    if (i != (int)blockIdx.x) __syncthreads();
+    const int4 t = __ldg(items + i);
+    const Dom<T>& D = doms[t.x];
+    div_sep_tile<T>(D.g, D.P[par], t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), D.use_Q, t.y, t.z);
+  }
 }
 
 template <typename T, typename SF, bool SOLID, bool UNIT>
 __global__ void __launch_bounds__(128, 6)
     k_collide_batch(const Dom<T>* __restrict__ doms, const int* __restrict__ start, int ndom, int par,
-                    int block0) {
+                    int block0, int nblocks) {
   // doms and start point at the first domain of a group of members; block0 is
-  // that domain's first block in the batch-wide numbering of start
-  const int blk = (int)blockIdx.x + block0;
-  const int d = find_domain(start, ndom, blk);
-  const Dom<T>& D = doms[d];
-  // domains hold fewer than 2^31 cells, so 32-bit unsigned index arithmetic is exact
-  const unsigned i = (unsigned)(blk - __ldg(start + d)) * 128u + threadIdx.x;
-  const unsigned nxy = (unsigned)D.g.nxy, nx = (unsigned)D.g.nx;
-  if (i >= nxy * (unsigned)D.g.nz) return;
-  const unsigned z = i / nxy, r = i - z * nxy, y = r / nx;
-  Cell c;
-  make_cell_at(D.g, (int)(r - y * nx), (int)y, (int)z, c);
-  collide_cell<T, SF, SOLID, UNIT>(D.g, D.P[par], D.ph, c);
+  // that domain's first 128-cell item in the batch-wide numbering of start;
+  // the group has nblocks items
+  for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
+    const int blk = b + block0;
+    const int d = find_domain(start, ndom, blk);
+    const Dom<T>& D = doms[d];
+    // domains hold fewer than 2^31 cells, so 32-bit unsigned index arithmetic is exact
+    const unsigned i = (unsigned)(blk - __ldg(start + d)) * 128u + threadIdx.x;
+    const unsigned nxy = (unsigned)D.g.nxy, nx = (unsigned)D.g.nx;
+    if (i >= nxy * (unsigned)D.g.nz) continue;
+    const unsigned z = i / nxy, r = i - z * nxy, y = r / nx;
+    Cell c;
+    make_cell_at(D.g, (int)(r - y * nx), (int)y, (int)z, c);
+    collide_cell<T, SF, SOLID, UNIT>(D.g, D.P[par], D.ph, c);
+  }
 }
 
 }  // namespace cg27

@@ -155,6 +155,44 @@ def test_batch_depth_does_not_change_results():
             assert np.array_equal(o[key], outs[0][key])
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_batch_grid_form_does_not_change_results(prec):
+    """One block per work item and the persistent grid (blocks walking the tile
+    list) give the same bits, with members of different sizes in several
+    groups, through chained and single steps."""
+    from paper_2309_07801_gb300 import cg
+    cases = [_case("osc", (48, 40, 24), 4.0, 0.005, 2), _case("static", (33, 30, 35), 2.0, 0.01, 3),
+             _case("osc", (64, 64, 64), 1.5, 0.008, 4)]
+    outs = []
+    for mode in (0, 1):
+        b = cg.Batch(4, prec)
+        b.set_depth(3)
+        b.set_persistent(mode)
+        doms = []
+        for params, fields in cases:
+            d = cg.Domain(cg.make_params(precision=prec, **params))
+            d.init(*fields)
+            b.add(d)
+            doms.append(d)
+        b.step(3)
+        b.step(9)
+        assert b.persistent == mode and b.depth == (3, False)
+        res = []
+        for d in doms:
+            b.remove(d)
+            res.append(d.macros())
+            d.close()
+        b.close()
+        outs.append(res)
+    for a, c in zip(*outs):
+        for key in a:
+            assert np.array_equal(a[key], c[key]), key
+    b = cg.Batch(1, prec)
+    with pytest.raises(cg.CGError):
+        b.set_persistent(2)
+    b.close()
+
+
 def test_batch_rules():
     from paper_2309_07801_gb300 import cg
     b = cg.Batch(2, "f32")

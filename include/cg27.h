@@ -236,7 +236,7 @@ int cg_destroy(cg_ctx *ctx);
 /* ---- batches: many domains advanced in shared launches -------------------
  * The paper has no counterpart: this is the library's way of running many
  * independent simulations (different sizes and parameters) at once.  The
- * members form up to sixteen contiguous groups of about equal cell counts; a
+ * members form up to four contiguous groups of about equal cell counts; a
  * batch step is four launches per group, each pass running over a work list
  * that concatenates the tiles of the group's members, with the arithmetic of
  * cg_step() for every cell.  A member's results are bitwise those of stepping

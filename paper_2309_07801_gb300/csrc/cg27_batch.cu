@@ -25,7 +25,7 @@ using namespace cg27;
 namespace {
 
 constexpr int TUNE_STEPS = 3;  // timed steps per candidate depth
-constexpr int BATCH_GROUPS = 16;  // member groups whose passes run concurrently (4..32 within 1 %)
+constexpr int BATCH_GROUPS = 4;  // member groups whose passes run concurrently (4..32 within 1 %)
 constexpr int BATCH_CHAIN = 8;   // steps per graph when enough steps are requested
 
 size_t dom_bytes(int precision) {
@@ -75,8 +75,10 @@ struct cg_batch {
   // member groups of the current table: members gdom[k] .. gdom[k+1]-1, tile
   // items gitem[k] .. gitem[k+1]-1, collision blocks cs[gdom[k]] .. cs[gdom[k+1]]-1
   std::vector<int> gdom, gitem, cs;
-  // graphs [one step | BATCH_CHAIN steps][parity of the first step]
+  // graphs [one step | BATCH_CHAIN steps][parity of the first step]; a stale
+  // graph is refreshed in place when the new one has the same shape
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  bool stale[2][2] = {{false, false}, {false, false}};
   bool use_graphs = true;
   // launch schedule: tile depth and grid form (0: one block per work item,
   // 1: persistent, a grid of the blocks the GPU holds at once walking the list)
@@ -104,13 +106,10 @@ struct cg_batch {
     }
   }
 
+  // the member set or the schedule changed: graphs are rebuilt at their next use
   void drop_graphs() {
-    for (auto& row : graph)
-      for (auto& g : row)
-        if (g) {
-          cudaGraphExecDestroy(g);
-          g = nullptr;
-        }
+    for (auto& row : stale)
+      for (bool& st : row) st = true;
   }
 };
 
@@ -267,7 +266,7 @@ void launch_step(cg_batch* b, int par) {
 
 // nsteps steps from parity par0: per group a chain of its four passes per step
 template <typename T, typename SF, bool SOLID, bool UNIT>
-cudaGraphExec_t build_batch_graph(const cg_batch* b, int par0, int nsteps) {
+cudaGraph_t build_batch_graph(const cg_batch* b, int par0, int nsteps) {
   cudaGraph_t gph;
   if (cudaGraphCreate(&gph, 0) != cudaSuccess) return nullptr;
   bool ok = true;
@@ -296,10 +295,34 @@ cudaGraphExec_t build_batch_graph(const cg_batch* b, int par0, int nsteps) {
       }
     }
   }
-  cudaGraphExec_t ex = nullptr;
-  if (!ok || cudaGraphInstantiate(&ex, gph, 0) != cudaSuccess) ex = nullptr;
-  cudaGraphDestroy(gph);
-  return ex;
+  if (!ok) {
+    cudaGraphDestroy(gph);
+    return nullptr;
+  }
+  return gph;
+}
+
+// the executable graph of slot (k, par) for the current table: refreshed in
+// place (cudaGraphExecUpdate: same nodes and edges, new grids and arguments)
+// when the member groups keep their number, else instantiated anew
+template <typename T, typename SF, bool SOLID, bool UNIT>
+bool ready_graph(cg_batch* b, int k, int par, int nsteps) {
+  cudaGraphExec_t& ex = b->graph[k][par];
+  if (ex && !b->stale[k][par]) return true;
+  cudaGraph_t g = build_batch_graph<T, SF, SOLID, UNIT>(b, par, nsteps);
+  if (!g) return false;
+  if (ex) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(ex, g, &info) != cudaSuccess) {
+      (void)cudaGetLastError();
+      cudaGraphExecDestroy(ex);
+      ex = nullptr;
+    }
+  }
+  if (!ex && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) ex = nullptr;
+  cudaGraphDestroy(g);
+  b->stale[k][par] = false;
+  return ex != nullptr;
 }
 
 template <typename T, typename SF, bool SOLID, bool UNIT>
@@ -318,12 +341,9 @@ int run_steps(cg_batch* b, int64_t n) {
     const int par = (int)(b->table_steps & 1);
     const int k = (n - s >= BATCH_CHAIN) ? 1 : 0;
     const int m = k ? BATCH_CHAIN : 1;
-    if (b->use_graphs && !b->graph[k][par]) {
-      b->graph[k][par] = build_batch_graph<T, SF, SOLID, UNIT>(b, par, m);
-      if (!b->graph[k][par]) {
-        (void)cudaGetLastError();
-        b->use_graphs = false;  // graphs unavailable here: plain launches from now on
-      }
+    if (b->use_graphs && !ready_graph<T, SF, SOLID, UNIT>(b, k, par, m)) {
+      (void)cudaGetLastError();
+      b->use_graphs = false;  // graphs unavailable here: plain launches from now on
     }
     if (b->use_graphs)
       CG_CUDA(cudaGraphLaunch(b->graph[k][par], b->stream));

@@ -85,8 +85,9 @@ class Server:
         total = torch.cuda.get_device_properties(self.device).total_memory
         self.hbm_budget = int(0.8 * total) if hbm_budget is None else int(hbm_budget)
         self.stream = torch.cuda.Stream(self.device)
-        # initialisation and read-back of the runs of a batch, beside its steps
-        self.io_stream = torch.cuda.Stream(self.device)
+        # initialisation and read-back of the runs of a batch, beside its steps;
+        # high priority, so that their small kernels get SMs while a quantum runs
+        self.io_stream = torch.cuda.Stream(self.device, priority=-1)
         self.batch = None
         if mode == "batched":
             self.batch = cg.Batch(self.max_active, precision, device=self.device, stream=self.stream)
@@ -130,17 +131,7 @@ class Server:
                 else:
                     for r in active:
                         r.dom.step(k)
-            # 2. meanwhile, read back the runs that finished before it
-            for r in leaving:
-                mass, dp, umax, flag, mac = _summary(r.req, r.dom, self.keep_macros)
-                fin = clock() - t0
-                results.append(Result(r.req.rid, r.req.edge, r.req.steps, r.req.arrival, r.admitted, fin,
-                                      r.mass0, mass, dp, umax, flag, mac))
-                used -= r.dom.nbytes
-                r.dom.close()
-                del r.dom
-            leaving = []
-            # ... and admit arrivals: a slot free and the workspace within the budget
+            # 2. meanwhile, admit arrivals (a slot free and the workspace within the budget) ...
             now = clock() - t0
             while i < len(pending) and pending[i].arrival <= now and len(active) + len(joining) < self.max_active:
                 need = cg.cg_workspace_bytes(cg.make_params(precision=self.precision,
@@ -151,6 +142,16 @@ class Server:
                 used += need
                 i += 1
                 now = clock() - t0
+            # ... and read back the runs that finished before it
+            for r in leaving:
+                mass, dp, umax, flag, mac = _summary(r.req, r.dom, self.keep_macros)
+                fin = clock() - t0
+                results.append(Result(r.req.rid, r.req.edge, r.req.steps, r.req.arrival, r.admitted, fin,
+                                      r.mass0, mass, dp, umax, flag, mac))
+                used -= r.dom.nbytes
+                r.dom.close()
+                del r.dom
+            leaving = []
             # 3. wait for the quantum and retire the runs it finished
             if k:
                 if self.batch is not None:

@@ -8,12 +8,8 @@ replayed from CUDA graphs); in the "per_run" mode each run is stepped with its
 own launches (cg_step), one run after the other, on the same stream.  Runs
 finish at different times; a finished run is read back (per-colour mass,
 pressure jump, largest velocity, non-finite flag) and its memory goes to the
-next arrivals.  In the batched mode the host work between quanta overlaps the
-GPU: the next quantum is enqueued first, and the read-backs of the runs that
-have just finished and the initialisation of new arrivals run meanwhile on a
-stream of their own (new arrivals join at the following quantum).  Time to
-result is measured from a request's arrival to the end of its read-back on the
-host clock.
+next arrivals.  Time to result is measured from a request's arrival to the end
+of its read-back on the host clock.
 """
 from __future__ import annotations
 
@@ -85,9 +81,6 @@ class Server:
         total = torch.cuda.get_device_properties(self.device).total_memory
         self.hbm_budget = int(0.8 * total) if hbm_budget is None else int(hbm_budget)
         self.stream = torch.cuda.Stream(self.device)
-        # initialisation and read-back of the runs of a batch, beside its steps;
-        # high priority, so that their small kernels get SMs while a quantum runs
-        self.io_stream = torch.cuda.Stream(self.device, priority=-1)
         self.batch = None
         if mode == "batched":
             self.batch = cg.Batch(self.max_active, precision, device=self.device, stream=self.stream)
@@ -102,9 +95,8 @@ class Server:
 
     def _admit(self, req, now) -> _Run:
         wl = req.workload()
-        stream = self.io_stream if self.batch is not None else self.stream
         dom = cg.Domain(cg.make_params(precision=self.precision, **wl.params()), device=self.device,
-                        stream=stream)
+                        stream=self.stream)
         dom.init(*req.fields())
         mass0, _ = dom.mass()
         if self.batch is not None:
@@ -112,65 +104,53 @@ class Server:
         return _Run(req, dom, 0, now, mass0)
 
     def run(self, requests, clock=time.perf_counter) -> dict:
+        import torch
         pending = sorted(requests, key=lambda r: r.arrival)
-        active: List[_Run] = []    # advanced by the quantum in flight
-        joining: List[_Run] = []   # admitted during it; advance from the next one
-        leaving: List[_Run] = []   # finished; read back during the next quantum
+        active: List[_Run] = []
         results: List[Result] = []
         used = 0
         cell_updates = 0
         t0 = clock()
         i = 0
-        while i < len(pending) or active or joining or leaving:
-            # 1. enqueue a quantum for the active runs (asynchronous)
-            k = 0
-            if active:
-                k = min(self.quantum, min(r.req.steps - r.done for r in active))
-                if self.batch is not None:
-                    self.batch.step(k)
-                else:
-                    for r in active:
-                        r.dom.step(k)
-            # 2. meanwhile, admit arrivals (a slot free and the workspace within the budget) ...
+        while i < len(pending) or active:
             now = clock() - t0
-            while i < len(pending) and pending[i].arrival <= now and len(active) + len(joining) < self.max_active:
+            # admission: arrived, a slot free, and the workspace fits the budget
+            while i < len(pending) and pending[i].arrival <= now and len(active) < self.max_active:
                 need = cg.cg_workspace_bytes(cg.make_params(precision=self.precision,
                                                             **pending[i].workload().params()))
                 if used + need > self.hbm_budget:
                     break
-                joining.append(self._admit(pending[i], now))
+                active.append(self._admit(pending[i], now))
                 used += need
                 i += 1
                 now = clock() - t0
-            # ... and read back the runs that finished before it
-            for r in leaving:
+            if not active:
+                if i < len(pending):
+                    time.sleep(max(0.0, min(0.05, pending[i].arrival - (clock() - t0))))
+                continue
+            k = min(self.quantum, min(r.req.steps - r.done for r in active))
+            if self.batch is not None:
+                self.batch.step(k)
+                self.batch.sync()
+            else:
+                for r in active:
+                    r.dom.step(k)
+                self.stream.synchronize()
+            for r in active:
+                r.done += k
+                cell_updates += k * r.req.cells
+            self.log.append((clock() - t0, len(active), k))
+            for r in [r for r in active if r.done >= r.req.steps]:
+                if self.batch is not None:
+                    self.batch.remove(r.dom)
                 mass, dp, umax, flag, mac = _summary(r.req, r.dom, self.keep_macros)
                 fin = clock() - t0
                 results.append(Result(r.req.rid, r.req.edge, r.req.steps, r.req.arrival, r.admitted, fin,
                                       r.mass0, mass, dp, umax, flag, mac))
+                active.remove(r)
                 used -= r.dom.nbytes
                 r.dom.close()
                 del r.dom
-            leaving = []
-            # 3. wait for the quantum and retire the runs it finished
-            if k:
-                if self.batch is not None:
-                    self.batch.sync()
-                else:
-                    self.stream.synchronize()
-                for r in active:
-                    r.done += k
-                    cell_updates += k * r.req.cells
-                self.log.append((clock() - t0, len(active), k))
-                for r in [r for r in active if r.done >= r.req.steps]:
-                    if self.batch is not None:
-                        self.batch.remove(r.dom)
-                    active.remove(r)
-                    leaving.append(r)
-            active += joining
-            joining = []
-            if not active and not leaving and i < len(pending):
-                time.sleep(max(0.0, min(0.05, pending[i].arrival - (clock() - t0))))
         wall = clock() - t0
         lat = np.array([r.latency for r in results])
         return {

@@ -251,16 +251,34 @@ GroupPass<T> group_pass(const cg_batch* b, int k) {
   return g;
 }
 
+// the four batch kernels of a variant in one grid form
+template <typename T, typename SF, bool SOLID, bool UNIT>
+void batch_kernels(bool persist, void* fn[4]) {
+  if (persist) {
+    fn[0] = (void*)k_macro_batch<T, SF, SOLID, true>;
+    fn[1] = (void*)k_fields_batch<T, SOLID, true>;
+    fn[2] = (void*)k_div_batch<T, true>;
+    fn[3] = (void*)k_collide_batch<T, SF, SOLID, UNIT, true>;
+  } else {
+    fn[0] = (void*)k_macro_batch<T, SF, SOLID, false>;
+    fn[1] = (void*)k_fields_batch<T, SOLID, false>;
+    fn[2] = (void*)k_div_batch<T, false>;
+    fn[3] = (void*)k_collide_batch<T, SF, SOLID, UNIT, false>;
+  }
+}
+
 template <typename T, typename SF, bool SOLID, bool UNIT>
 void launch_step(cg_batch* b, int par) {
-  const dim3 blk(TX, TY, 1);
+  const dim3 blk(TX, TY, 1), cblk(128, 1, 1);
+  void* fn[4];
+  batch_kernels<T, SF, SOLID, UNIT>(b->persist != 0, fn);
   for (int k = 0; k + 1 < (int)b->gdom.size(); ++k) {
-    const GroupPass<T> g = group_pass<T>(b, k);
-    k_macro_batch<T, SF, SOLID><<<g.grid[0], blk, 0, b->stream>>>(g.doms, g.items, g.ntiles, par);
-    k_fields_batch<T, SOLID><<<g.grid[1], blk, 0, b->stream>>>(g.doms, g.items, g.ntiles, par);
-    k_div_batch<T><<<g.grid[2], blk, 0, b->stream>>>(g.doms, g.items, g.ntiles, par);
-    k_collide_batch<T, SF, SOLID, UNIT><<<g.grid[3], 128, 0, b->stream>>>(g.cdoms, g.cs, g.ndom, par, g.block0,
-                                                                         g.nblocks);
+    GroupPass<T> g = group_pass<T>(b, k);
+    void* a_tile[] = {(void*)&g.doms, (void*)&g.items, (void*)&g.ntiles, (void*)&par};
+    void* a_coll[] = {(void*)&g.cdoms, (void*)&g.cs, (void*)&g.ndom, (void*)&par, (void*)&g.block0,
+                      (void*)&g.nblocks};
+    for (int p = 0; p < 4; ++p)
+      cudaLaunchKernel(fn[p], g.grid[p], p < 3 ? blk : cblk, p < 3 ? a_tile : a_coll, 0, b->stream);
   }
 }
 
@@ -273,8 +291,8 @@ cudaGraph_t build_batch_graph(const cg_batch* b, int par0, int nsteps) {
   const dim3 blk(TX, TY, 1), cblk(128, 1, 1);
   const int ng = (int)b->gdom.size() - 1;
   std::vector<cudaGraphNode_t> last(ng, nullptr);
-  void* fn[4] = {(void*)k_macro_batch<T, SF, SOLID>, (void*)k_fields_batch<T, SOLID>, (void*)k_div_batch<T>,
-                 (void*)k_collide_batch<T, SF, SOLID, UNIT>};
+  void* fn[4];
+  batch_kernels<T, SF, SOLID, UNIT>(b->persist != 0, fn);
   for (int s = 0; s < nsteps && ok; ++s) {
     int par = (par0 + s) & 1;
     for (int k = 0; k < ng && ok; ++k) {
@@ -332,8 +350,8 @@ int run_steps(cg_batch* b, int64_t n) {
     int dev = 0;
     CG_CUDA(cudaGetDevice(&dev));
     CG_CUDA(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev));
-    const void* fn[4] = {(const void*)k_macro_batch<T, SF, SOLID>, (const void*)k_fields_batch<T, SOLID>,
-                         (const void*)k_div_batch<T>, (const void*)k_collide_batch<T, SF, SOLID, UNIT>};
+    void* fn[4];
+    batch_kernels<T, SF, SOLID, UNIT>(true, fn);
     for (int p = 0; p < 4; ++p)
       CG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->resident[p], fn[p], p < 3 ? NT : 128, 0));
   }

@@ -801,64 +801,98 @@ __device__ __forceinline__ int find_domain(const int* __restrict__ start, int nd
 }
 
 // Tiles of a z-marching batch pass: item i = (domain, tile x, tile y, z chunk).
-// A block that takes several tiles waits at a barrier before each further one,
-// so the next tile's shared-memory prologue follows the last reads of the
-// previous tile.
+// PERSIST = false: block b runs item b.  PERSIST = true: block b runs items b,
+// b + gridDim.x, ..., waiting at a barrier before each further one, so the
+// next tile's shared-memory prologue follows the last reads of the previous
+// tile.  (The two forms are separate instantiations: the loop costs the
+// one-item form about 5 % when it is compiled in.)
 template <typename T, typename SF, bool SOLID>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !SOLID) ? 4 : 1)
-    k_macro_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int nitems, int par) {
-  for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
-    if (i != (int)blockIdx.x) __syncthreads();
-    const int4 t = __ldg(items + i);
-    const Dom<T>& D = doms[t.x];
-    macro_tile<T, SF, SOLID>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
-  }
+__device__ __forceinline__ void macro_item(const Dom<T>* __restrict__ doms, int4 t, int par) {
+  const Dom<T>& D = doms[t.x];
+  macro_tile<T, SF, SOLID>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
 }
 
 template <typename T, bool SOLID>
-__global__ void __launch_bounds__(NT)
-    k_fields_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int nitems, int par) {
-  for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
-    if (i != (int)blockIdx.x) __syncthreads();
-    const int4 t = __ldg(items + i);
-    const Dom<T>& D = doms[t.x];
-    if constexpr (!SOLID && sizeof(T) == 4)
-      fields_sep_tile<T>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
-    else
-      fields_tile<T, SOLID>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
-  }
+__device__ __forceinline__ void fields_item(const Dom<T>* __restrict__ doms, int4 t, int par) {
+  const Dom<T>& D = doms[t.x];
+  if constexpr (!SOLID && sizeof(T) == 4)
+    fields_sep_tile<T>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
+  else
+    fields_tile<T, SOLID>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT)
-    k_div_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int nitems, int par) {
-  for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
-    if (i != (int)blockIdx.x) __syncthreads();
-    const int4 t = __ldg(items + i);
-    const Dom<T>& D = doms[t.x];
-    div_sep_tile<T>(D.g, D.P[par], t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), D.use_Q, t.y, t.z);
+__device__ __forceinline__ void div_item(const Dom<T>* __restrict__ doms, int4 t, int par) {
+  const Dom<T>& D = doms[t.x];
+  div_sep_tile<T>(D.g, D.P[par], t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), D.use_Q, t.y, t.z);
+}
+
+template <typename T, typename SF, bool SOLID, bool PERSIST>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !SOLID) ? 4 : 1)
+    k_macro_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int nitems, int par) {
+  if constexpr (!PERSIST) {
+    macro_item<T, SF, SOLID>(doms, __ldg(items + blockIdx.x), par);
+  } else {
+    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+      if (i != (int)blockIdx.x) __syncthreads();
+      macro_item<T, SF, SOLID>(doms, __ldg(items + i), par);
+    }
   }
 }
 
+template <typename T, bool SOLID, bool PERSIST>
+__global__ void __launch_bounds__(NT)
+    k_fields_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int nitems, int par) {
+  if constexpr (!PERSIST) {
+    fields_item<T, SOLID>(doms, __ldg(items + blockIdx.x), par);
+  } else {
+    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+      if (i != (int)blockIdx.x) __syncthreads();
+      fields_item<T, SOLID>(doms, __ldg(items + i), par);
+    }
+  }
+}
+
+template <typename T, bool PERSIST>
+__global__ void __launch_bounds__(NT)
+    k_div_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int nitems, int par) {
+  if constexpr (!PERSIST) {
+    div_item<T>(doms, __ldg(items + blockIdx.x), par);
+  } else {
+    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+      if (i != (int)blockIdx.x) __syncthreads();
+      div_item<T>(doms, __ldg(items + i), par);
+    }
+  }
+}
+
+// collision item blk (batch-wide numbering of start): 128 cells of one domain
 template <typename T, typename SF, bool SOLID, bool UNIT>
+__device__ __forceinline__ void collide_item(const Dom<T>* __restrict__ doms, const int* __restrict__ start,
+                                             int ndom, int par, int blk) {
+  const int d = find_domain(start, ndom, blk);
+  const Dom<T>& D = doms[d];
+  // domains hold fewer than 2^31 cells, so 32-bit unsigned index arithmetic is exact
+  const unsigned i = (unsigned)(blk - __ldg(start + d)) * 128u + threadIdx.x;
+  const unsigned nxy = (unsigned)D.g.nxy, nx = (unsigned)D.g.nx;
+  if (i >= nxy * (unsigned)D.g.nz) return;
+  const unsigned z = i / nxy, r = i - z * nxy, y = r / nx;
+  Cell c;
+  make_cell_at(D.g, (int)(r - y * nx), (int)y, (int)z, c);
+  collide_cell<T, SF, SOLID, UNIT>(D.g, D.P[par], D.ph, c);
+}
+
+// doms and start point at the first domain of a group of members; block0 is
+// that domain's first 128-cell item in the batch-wide numbering of start; the
+// group has nblocks items
+template <typename T, typename SF, bool SOLID, bool UNIT, bool PERSIST>
 __global__ void __launch_bounds__(128, 6)
     k_collide_batch(const Dom<T>* __restrict__ doms, const int* __restrict__ start, int ndom, int par,
                     int block0, int nblocks) {
-  // doms and start point at the first domain of a group of members; block0 is
-  // that domain's first 128-cell item in the batch-wide numbering of start;
-  // the group has nblocks items
-  for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
-    const int blk = b + block0;
-    const int d = find_domain(start, ndom, blk);
-    const Dom<T>& D = doms[d];
-    // domains hold fewer than 2^31 cells, so 32-bit unsigned index arithmetic is exact
-    const unsigned i = (unsigned)(blk - __ldg(start + d)) * 128u + threadIdx.x;
-    const unsigned nxy = (unsigned)D.g.nxy, nx = (unsigned)D.g.nx;
-    if (i >= nxy * (unsigned)D.g.nz) continue;
-    const unsigned z = i / nxy, r = i - z * nxy, y = r / nx;
-    Cell c;
-    make_cell_at(D.g, (int)(r - y * nx), (int)y, (int)z, c);
-    collide_cell<T, SF, SOLID, UNIT>(D.g, D.P[par], D.ph, c);
+  if constexpr (!PERSIST) {
+    collide_item<T, SF, SOLID, UNIT>(doms, start, ndom, par, (int)blockIdx.x + block0);
+  } else {
+    for (int b = blockIdx.x; b < nblocks; b += gridDim.x) collide_item<T, SF, SOLID, UNIT>(doms, start, ndom, par, b + block0);
   }
 }
 

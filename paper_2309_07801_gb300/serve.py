@@ -52,16 +52,39 @@ class _Run:
     mass0: np.ndarray
 
 
+_R2 = {}  # squared distance to the centre of an edge^3 box, per edge
+
+
+def _r2(n: int) -> np.ndarray:
+    if n not in _R2:
+        d = (np.arange(n) - n / 2.0) ** 2
+        _R2[n] = d[:, None, None] + d[None, :, None] + d[None, None, :]
+    return _R2[n]
+
+
+def diagnostics(n: int, radius: float, p: np.ndarray, u: np.ndarray):
+    """Pressure jump (mean p inside half the radius minus mean p beyond the
+    radius plus a quarter edge, about the box centre) and largest |u| of a
+    droplet run in an n^3 box (p as [z, y, x], u as [3, z, y, x])."""
+    r2 = _r2(n)
+    inner = r2 < (0.5 * radius) ** 2
+    outer = r2 > (radius + 0.25 * n) ** 2
+    p = p.reshape(n, n, n)
+    dp = float(p[inner].mean() - p[outer].mean()) if inner.any() and outer.any() else float("nan")
+    return dp, float(np.abs(u).max())
+
+
 def _summary(req, dom: cg.Domain, keep_macros: bool):
-    m = dom.macros()
+    if keep_macros:
+        m = dom.macros()
+        p, u = m["p"], m["u"]
+    else:  # only what the summary needs
+        m = None
+        p, u = np.empty(dom.N), np.empty(3 * dom.N)
+        cg.cg_read_macros(dom.h, u=u, p=p)
     mass, flag = dom.mass()
-    n = req.edge
-    c = n / 2.0
-    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
-    r = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2)
-    inner, outer = r < 0.5 * req.radius, r > req.radius + 0.25 * n
-    dp = float(m["p"][inner].mean() - m["p"][outer].mean()) if inner.any() and outer.any() else float("nan")
-    return mass, float(dp), float(np.abs(m["u"]).max()), flag, (m if keep_macros else None)
+    dp, umax = diagnostics(req.edge, req.radius, p, u)
+    return mass, dp, umax, flag, m
 
 
 class Server:

@@ -8,8 +8,12 @@ replayed from CUDA graphs); in the "per_run" mode each run is stepped with its
 own launches (cg_step), one run after the other, on the same stream.  Runs
 finish at different times; a finished run is read back (per-colour mass,
 pressure jump, largest velocity, non-finite flag) and its memory goes to the
-next arrivals.  Time to result is measured from a request's arrival to the end
-of its read-back on the host clock.
+next arrivals.  In the batched mode admission overlaps the GPU: before a
+quantum the server admits arrived requests for at most ADMIT_SLICE seconds of
+host time (at least one when the GPU would otherwise idle), and while the
+quantum runs it admits further arrivals as long as the GPU is still busy; runs
+admitted during a quantum join the next one.  Time to result is measured from a
+request's arrival to the end of its read-back on the host clock.
 """
 from __future__ import annotations
 
@@ -87,6 +91,9 @@ def _summary(req, dom: cg.Domain, keep_macros: bool):
     return mass, dp, umax, flag, m
 
 
+ADMIT_SLICE = 0.02  # seconds of admission work before a quantum (batched mode)
+
+
 class Server:
     """mode: "batched" (shared launches) or "per_run" (one run's launches at a
     time).  hbm_budget: bytes of workspace the active runs may hold (default:
@@ -104,6 +111,8 @@ class Server:
         total = torch.cuda.get_device_properties(self.device).total_memory
         self.hbm_budget = int(0.8 * total) if hbm_budget is None else int(hbm_budget)
         self.stream = torch.cuda.Stream(self.device)
+        # initialisation of the runs of a batch, beside the batch's steps
+        self.io_stream = torch.cuda.Stream(self.device)
         self.batch = None
         if mode == "batched":
             self.batch = cg.Batch(self.max_active, precision, device=self.device, stream=self.stream)
@@ -118,8 +127,9 @@ class Server:
 
     def _admit(self, req, now) -> _Run:
         wl = req.workload()
+        stream = self.io_stream if self.batch is not None else self.stream
         dom = cg.Domain(cg.make_params(precision=self.precision, **wl.params()), device=self.device,
-                        stream=self.stream)
+                        stream=stream)
         dom.init(*req.fields())
         mass0, _ = dom.mass()
         if self.batch is not None:
@@ -127,26 +137,39 @@ class Server:
         return _Run(req, dom, 0, now, mass0)
 
     def run(self, requests, clock=time.perf_counter) -> dict:
-        import torch
         pending = sorted(requests, key=lambda r: r.arrival)
-        active: List[_Run] = []
+        active: List[_Run] = []    # advanced by the next quantum
+        joining: List[_Run] = []   # admitted while a quantum runs
         results: List[Result] = []
         used = 0
         cell_updates = 0
         t0 = clock()
         i = 0
-        while i < len(pending) or active:
-            now = clock() - t0
-            # admission: arrived, a slot free, and the workspace fits the budget
-            while i < len(pending) and pending[i].arrival <= now and len(active) < self.max_active:
+
+        def admit(go_on):
+            """Admit arrived requests while a slot is free, the workspace fits
+            the budget and go_on(number admitted so far) holds."""
+            nonlocal i, used
+            n = 0
+            while i < len(pending) and pending[i].arrival <= clock() - t0 and \
+                    len(active) + len(joining) < self.max_active and go_on(n):
                 need = cg.cg_workspace_bytes(cg.make_params(precision=self.precision,
                                                             **pending[i].workload().params()))
                 if used + need > self.hbm_budget:
                     break
-                active.append(self._admit(pending[i], now))
+                joining.append(self._admit(pending[i], clock() - t0))
                 used += need
                 i += 1
-                now = clock() - t0
+                n += 1
+
+        while i < len(pending) or active or joining:
+            if self.batch is not None:
+                start = clock()
+                admit(lambda n: n == 0 or clock() - start < ADMIT_SLICE)
+            else:
+                admit(lambda n: True)
+            active += joining
+            joining = []
             if not active:
                 if i < len(pending):
                     time.sleep(max(0.0, min(0.05, pending[i].arrival - (clock() - t0))))
@@ -154,6 +177,8 @@ class Server:
             k = min(self.quantum, min(r.req.steps - r.done for r in active))
             if self.batch is not None:
                 self.batch.step(k)
+                # the GPU is busy with the quantum: admit meanwhile
+                admit(lambda n: not self.stream.query())
                 self.batch.sync()
             else:
                 for r in active:

@@ -164,7 +164,15 @@ int cg_create(const cg_params *p, void *d_workspace, size_t bytes,
 int cg_init_fields(cg_ctx *ctx, const double *rho_r, const double *rho_b,
                    const double *u, const uint8_t *solid);
 
-/* Advance nsteps (>= 0) time steps, enqueued on the domain's stream. */
+/* Advance nsteps (>= 0) time steps, enqueued on the domain's stream
+ * (asynchronous; returns after enqueueing).  A D3Q27 domain with nz >= 32 runs
+ * as CUDA graphs of per-slab kernels (16-plane z slabs, the passes of
+ * neighbouring slabs and of up to eight consecutive steps overlapping under
+ * their data dependencies), built on first use per chain length and step
+ * parity; while per-pass timing is on (cg_profile_enable) or the stream is
+ * being captured by the caller, each pass is one plain launch instead.  The
+ * results are the same either way, bit for bit.  CG_ERR_INVALID_ARG for a
+ * negative count, a domain not initialised, or a member of a batch. */
 int cg_step(cg_ctx *ctx, int64_t nsteps);
 
 /* Copy the fields of the latest post-streaming state to host arrays (each may

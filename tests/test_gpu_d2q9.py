@@ -135,3 +135,37 @@ def test_d2q9_laplace_table():
     for ratio, s_th, s_cal, s_cal_paper, e, e_paper in results:
         assert abs(s_cal - s_cal_paper) <= 5e-3 * s_th, results
         assert abs(e - e_paper) <= 0.5, results
+
+
+@pytest.mark.parametrize("case,steps,wall_tol,l2_tol", [("A", 60000, 2e-3, 0.10), ("B", 400000, 5e-3, 0.05)])
+def test_d2q9_layered_flow_at_the_paper_size(case, steps, wall_tol, l2_tol):
+    """The layered flow of Sec. IV.C (Cases A and B of its table) in a
+    100-cell channel between bounce-back walls, FP64 on the GPU: the layer
+    along the walls follows the analytic piecewise-parabolic profile and the
+    channel's L2 error stays within the bounds the oracle meets on the CPU."""
+    from paper_2309_07801_gb300 import cg
+    rr0, rb0, ab = {"A": (0.1, 0.8, 0.9), "B": (0.8, 0.1, 0.2)}[case]
+    ar = 1 - (1 - ab) / (rr0 / rb0)
+    H, nu, G = 100, 0.1, 1.5e-8
+    nx, ny, b = 4, H + 2, H / 2.0
+    a = b / 2.0
+    yc = (ny - 1) / 2.0
+    phi0 = np.tanh(2.0 * (a - np.abs(np.arange(ny) - yc)) / 4.0)
+    rr = np.repeat((rr0 * (1 + phi0) / 2)[:, None], nx, axis=1)[None]
+    rb = np.repeat((rb0 * (1 - phi0) / 2)[:, None], nx, axis=1)[None]
+    d = cg.Domain(cg.make_params(nx, ny, 1, lattice=cg.CG_D2Q9, precision="f64", bc=(0, 1, 0),
+                                 rho_r0=rr0, rho_b0=rb0, alpha_r=ar, alpha_b=ab, nu_r=nu, nu_b=nu,
+                                 sigma=0.002 / 4.5, beta=0.7, force_mode=1, g=(G, 0.0, 0.0)))
+    d.init(rr, rb, np.zeros((3, 1, ny, nx)))
+    d.step(steps)
+    ux = d.macros()["u"][0, 0, 1:-1, :]
+    d.close()
+    assert np.abs(ux - ux[:, :1]).max() < 1e-15  # the flow does not depend on x
+    ux = ux[:, 0]
+    y = np.arange(1, ny - 1) - yc
+    A1, A2 = -G / (2 * rr0 * nu), -G / (2 * rb0 * nu)
+    C1, C2 = (A2 - A1) * a * a - A2 * b * b, -A2 * b * b
+    ref = np.where(np.abs(y) <= a, A1 * y * y + C1, A2 * y * y + C2)
+    outer = np.abs(y) >= a + 3
+    assert np.abs(ux - ref)[outer].max() / ref.max() < wall_tol
+    assert np.linalg.norm(ux - ref) / np.linalg.norm(ref) < l2_tol

@@ -273,8 +273,8 @@ int cg_batch_workspace_bytes(int32_t max_domains, int32_t precision, size_t *byt
 /* Create an empty batch.  d_workspace: device pointer of at least
  * cg_batch_workspace_bytes() bytes, 256-byte aligned, owned by the caller and
  * kept alive until cg_batch_destroy().  cuda_stream: the stream all batch
- * launches go to (NULL = legacy default stream, which cannot be captured:
- * plain launches are used then). */
+ * launches go to (NULL = the legacy default stream; the batch then uses plain
+ * launches instead of graphs). */
 int cg_batch_create(int32_t max_domains, int32_t precision, void *d_workspace, size_t bytes,
                     void *cuda_stream, cg_batch **out);
 

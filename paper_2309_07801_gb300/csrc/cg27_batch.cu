@@ -460,7 +460,7 @@ int cg_batch_create(int32_t max_domains, int32_t precision, void* d_workspace, s
   b->ws = static_cast<char*>(d_workspace);
   b->L = batch_layout(max_domains, precision, table_items(max_domains));
   b->stream = static_cast<cudaStream_t>(cuda_stream);
-  b->use_graphs = b->stream != nullptr;  // the legacy default stream cannot be captured
+  b->use_graphs = b->stream != nullptr;  // plain launches on the legacy default stream
   if (cudaEventCreate(&b->ev[0]) != cudaSuccess || cudaEventCreate(&b->ev[1]) != cudaSuccess) {
     delete b;
     return fail(CG_ERR_CUDA, "cudaEventCreate failed");

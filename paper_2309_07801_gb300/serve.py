@@ -155,6 +155,9 @@ class Server:
                     len(active) + len(joining) < self.max_active and go_on(n):
                 need = cg.cg_workspace_bytes(cg.make_params(precision=self.precision,
                                                             **pending[i].workload().params()))
+                if need > self.hbm_budget:
+                    raise ValueError("request %d needs %d bytes of workspace, more than the budget of %d"
+                                     % (pending[i].rid, need, self.hbm_budget))
                 if used + need > self.hbm_budget:
                     break
                 joining.append(self._admit(pending[i], clock() - t0))

@@ -142,3 +142,47 @@ def test_model_catches_a_missing_edge():
     bad = [(u, v) for u, v in itertools.combinations(sorted(acc), 2)
            if (acc[u][1] & (acc[v][0] | acc[v][1]) or acc[v][1] & acc[u][0]) and u not in anc[v]]
     assert bad
+
+
+def test_in_place_slot_rules_on_a_3d_lattice():
+    """The in-place rules of cg27.h on a periodic 4 x 3 x 5 D3Q27 lattice: in
+    each step every slot is read by exactly one cell and written by that same
+    cell; and tracing values through an even and an odd step gives the pull
+    of the two-buffer scheme (cell x receives, for direction q, the value its
+    neighbour x - c_q emitted in the previous step)."""
+    nx, ny, nz = 4, 3, 5
+    dirs = [(cx, cy, cz) for cz in (-1, 0, 1) for cy in (-1, 0, 1) for cx in (-1, 0, 1)]
+    opp = lambda q: 26 - q
+    cells = [(x, y, z) for z in range(nz) for y in range(ny) for x in range(nx)]
+    add = lambda a, c, s=1: ((a[0] + s * c[0]) % nx, (a[1] + s * c[1]) % ny, (a[2] + s * c[2]) % nz)
+    assert all(dirs[opp(q)] == tuple(-v for v in dirs[q]) for q in range(27))
+
+    def slots(step, cell):
+        rd = {q: ((q, cell) if step % 2 == 0 else (opp(q), add(cell, dirs[q], -1))) for q in range(27)}
+        wr = {q: ((opp(q), cell) if step % 2 == 0 else (q, add(cell, dirs[q]))) for q in range(27)}
+        return rd, wr
+
+    for step in (0, 1):
+        readers, writers = {}, {}
+        for cell in cells:
+            rd, wr = slots(step, cell)
+            for s in rd.values():
+                readers.setdefault(s, []).append(cell)
+            for s in wr.values():
+                writers.setdefault(s, []).append(cell)
+        assert len(readers) == len(writers) == 27 * len(cells)
+        for s, who in readers.items():
+            assert len(who) == 1 and writers[s] == who
+    # values: before an even step, slot (q, x + c_q) holds what cell x emitted for
+    # q (the layout the initialisation writes); run four steps
+    mem = {(q, add(cell, dirs[q])): ("init", cell, q) for cell in cells for q in range(27)}
+    for step in range(4):
+        new = dict(mem)
+        for cell in cells:
+            rd, wr = slots(step, cell)
+            got = {q: mem[rd[q]] for q in range(27)}
+            for q in range(27):
+                tag, src, qq = got[q]
+                assert qq == q and src == add(cell, dirs[q], -1), (step, cell, q, got[q])
+                new[wr[q]] = (step, cell, q)
+        mem = new

@@ -170,3 +170,25 @@ def test_in_place_streaming_validation(cg):
         with pytest.raises(cg.CGError) as e:
             cg.cg_workspace_bytes(p)
         assert e.value.code == -1
+
+
+def test_batch_entry_points_validate_without_a_gpu(cg):
+    """The batch calls reject bad arguments before touching the device."""
+    L = cg.lib()
+    n = ctypes.c_size_t(0)
+    assert L.cg_batch_workspace_bytes(8, cg.CG_F32, ctypes.byref(n)) == 0 and n.value > 0
+    small = n.value
+    assert L.cg_batch_workspace_bytes(64, cg.CG_F32, ctypes.byref(n)) == 0 and n.value >= small
+    for bad in ((0, cg.CG_F32), ((1 << 20) + 1, cg.CG_F32)):
+        assert L.cg_batch_workspace_bytes(bad[0], bad[1], ctypes.byref(n)) == -1
+    assert L.cg_batch_workspace_bytes(4, 7, ctypes.byref(n)) == -2       # unknown precision
+    assert L.cg_batch_workspace_bytes(4, cg.CG_F32, None) == -1
+    out = ctypes.c_void_p()
+    assert L.cg_batch_create(4, cg.CG_F32, None, 1 << 20, None, ctypes.byref(out)) == -5  # no workspace
+    i32 = ctypes.c_int32(0)
+    for rc in (L.cg_batch_step(None, 1), L.cg_batch_sync(None), L.cg_batch_set_depth(None, 2),
+               L.cg_batch_set_persistent(None, 0), L.cg_batch_persistent(None, ctypes.byref(i32)),
+               L.cg_batch_size(None, ctypes.byref(i32)), L.cg_batch_add(None, None),
+               L.cg_batch_remove(None, None), L.cg_batch_destroy(None)):
+        assert rc == -1
+    assert "NULL" in cg.cg_last_error() or "batch" in cg.cg_last_error()

@@ -18,6 +18,7 @@ Everything here runs through the CUDA library; the CPU oracle is not used.
     python -m paper_2309_07801_gb300.studies bubble --steps 20000 --every 2000 --precisions f32,f64
     python -m paper_2309_07801_gb300.studies collision --edge 512 --steps 10000 --every 2000
     python -m paper_2309_07801_gb300.studies rti --edge 128 --steps 9600 --every 800 --model D
+    python -m paper_2309_07801_gb300.studies rti --edge 64 --steps 6400 --every 800 --model C --re inf
 """
 from __future__ import annotations
 
@@ -224,6 +225,7 @@ def main(argv=None):
     ap.add_argument("--every", type=int, default=500)
     ap.add_argument("--precisions", default="f32")
     ap.add_argument("--case", default="config", choices=["config", "case2"])
+    ap.add_argument("--re", type=float, default=1024.0, help="Reynolds number of the RTI (inf: nu = 0)")
     args = ap.parse_args(argv)
     from . import build
     build.build()
@@ -236,7 +238,8 @@ def main(argv=None):
             print(json.dumps(bubble(args.steps, args.every, p, case=args.case)), flush=True)
     elif args.study == "rti":
         for p in precs:
-            print(json.dumps(rti(args.edge, args.steps, args.every, p, "ABCD".index(args.model))), flush=True)
+            print(json.dumps(rti(args.edge, args.steps, args.every, p, "ABCD".index(args.model), args.re)),
+                  flush=True)
     else:
         for r in collision(args.edge, args.steps, args.every, tuple(precs)):
             print(json.dumps(r), flush=True)

@@ -16,8 +16,7 @@
  *   - recoloring of Sec. II.A (Eqs. recoloring and R), pull streaming, and
  *     fullway bounce-back at solid cells (Sec. IV).
  *
- * Readings of points the paper leaves open (each is also listed in the design
- * notes of the repository):
+ * Readings of points the paper leaves open:
  *   - (c_s^k)^2 = xi (1 - alpha_k) (the stray rho_k in Sec. II.A dropped);
  *   - the lattice c_s^2 = 1/3 everywhere except the equation of state;
  *   - Q_a = -3 d_a[(p - rho c_s^2) u_a] component by component (Sec. III.E);

@@ -1,24 +1,29 @@
 #!/usr/bin/env python3
 """Throughput of the D3Q27 colour-gradient CM-MRT time step on GB300.
 
-Workload: the translating droplet, 128^3 periodic cells, density ratio 10
-(rho_r0 = 1, rho_b0 = 0.1), R = 20, nu = 0.05, sigma = 0.005, beta = 0.7,
-initial velocity (0.05, 0.05, 0), FP32 storage and arithmetic.  One bench step
-is one lattice time step over the whole domain; the metric is million lattice
-updates per second (MLUPS).  With --gpus N (launched by torchrun) every rank
-advances its own independent replica (the method shards into independent
-domains only, so there is no collective on the data path; scaling is weak).
+Headline workload: the head-on binary droplet collision, 512^3 periodic cells,
+two droplets of radius 48 at x = 256 -+ 56 closing at a relative speed of 0.2,
+density ratio 1, nu = 0.002 (Re ~ 4800), sigma = 0.005, beta = 0.7, FP32
+storage and arithmetic, two population buffers.  One bench step is one
+lattice time step over the whole domain; the metric is million lattice
+updates per second (MLUPS).  --workload translating selects the translating
+droplet (128^3, ratio 10) instead.  With --gpus N (launched by torchrun) every
+rank advances its own independent replica (the method shards into
+independent domains only, so there is no collective on the data path;
+scaling is weak).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-The line also carries the same workload in the 16-bit storage modes and with
-in-place streaming ("variants": MLUPS and workspace bytes of each), and a
-serving measurement ("serving"): 256 independent static
-or oscillating droplet runs (edges 32..128, ratio 1..10, 500..5000 steps) with
-Poisson arrivals, admitted by free device memory and advanced together in
-shared launches (continuous batching); it reports p50/p99 time to result,
-runs per hour and the aggregate MLUPS.  --serve-compare adds the same requests
-arriving at once, served batched and with one set of launches per run.
+The line reports the step against the HBM roofline first (the paper layout's
+432 B per cell update and this layout's own 248 B), then the dominant kernel's
+roofline and each pass's own fraction.  It also carries the same workloads in
+the 16-bit storage modes and with in-place streaming ("variants"), and a
+serving measurement ("serving"): 256 independent static or oscillating
+droplet runs (edges 32..128, ratio 1..10, 500..5000 steps) with Poisson
+arrivals, admitted by free device memory and advanced together in shared
+launches (continuous batching), with p50/p99 time to result, runs per hour
+and the aggregate MLUPS; the same requests arriving at once are served
+batched and with one set of launches per run, beside the single-domain rate.
 
 The reference arm times the FP64 CPU oracle as it stands on the host cores, on
 a bounded periodic slab of the same workload per step.
@@ -43,27 +48,36 @@ if ROOT not in sys.path:
 METRIC = "D3Q27 CG-CM MLUPS"
 UNIT = "MLUPS"
 STEP_BYTES_432 = 432          # paper layout: 2 colours x 27 FP32 populations, read + write
+STATE_BYTES_248 = 248         # this layout: 27 FP32 totals + 4 scalars, read + write
 COLLIDE_BYTES_PER_CELL = 248  # k_collide: f in (108) + rho_r, rho_b (8) + F (12) + Q (12) + f out (108)
+# algorithmic bytes per cell of each pass (FP32, periodic; every field read or written once)
+PASS_BYTES = {"k_macro": 144, "k_fields": 68, "k_div": 40, "k_collide": 248}
+GRAPH_STEPS = 8               # steps chained in one slab graph of the library
 
 
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--edge", type=int, default=128)
+    ap.add_argument("--workload", choices=["collision", "translating"], default="collision")
+    ap.add_argument("--edge", type=int, default=0, help="domain edge (default 512 collision, 128 translating)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-serve-compare", action="store_true",
+                    help="skip the burst comparison (batched vs one set of launches per run)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other storage modes and in-place streaming")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-rate", type=float, default=3.8,
                     help="Poisson arrivals per second (about 0.8 of the batched capacity)")
-    ap.add_argument("--serve-compare", action="store_true",
-                    help="also serve all requests arriving at once, batched and per run")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.edge <= 0:
+        args.edge = 512 if args.workload == "collision" else 128
+    return args
 
 
 def load_peaks():
@@ -107,13 +121,32 @@ def step_slabs(nz, planes=16):
     return (nz + planes - 1) // planes if nz >= 2 * planes else 1
 
 
-def workload(edge):
+def make_workload(kind, edge):
     from paper_2309_07801_gb300 import inputs
-    wl = inputs.translating_droplet(edge)
-    return wl, inputs.workload_fields(wl)
+    if kind == "collision":
+        return inputs.droplet_collision(edge)
+    return inputs.translating_droplet(edge)
+
+
+def workload_fields(wl, z_range=None):
+    """Initial fields of the workload, or of the planes z_range of it."""
+    from paper_2309_07801_gb300 import inputs
+    if wl.name.startswith("droplet_collision"):
+        return inputs.collision_fields(wl, z_range)
+    rr, rb, u = inputs.workload_fields(wl)
+    if z_range is None:
+        return rr, rb, u
+    sl = slice(*z_range)
+    return (np.ascontiguousarray(rr[sl]), np.ascontiguousarray(rb[sl]),
+            np.ascontiguousarray(u[:, sl]))
 
 
 def describe(wl):
+    if wl.name.startswith("droplet_collision"):
+        n = wl.nx
+        return ("head-on droplet collision %d^3 periodic, two droplets R=%g at x=%g-+%g closing at 0.2, "
+                "ratio 1, nu=0.002 (Re~4800), sigma=0.005, beta=0.7, Model D, Q on"
+                % (n, 48.0 * n / 512.0, n / 2.0, 56.0 * n / 512.0))
     return ("translating droplet %d^3 periodic, ratio 10 (1:0.1), R=%g, nu=0.05, sigma=0.005, "
             "beta=0.7, u0=(0.05,0.05,0), Model D, Q on" % (wl.nx, 20.0 * wl.nx / 128.0))
 
@@ -215,20 +248,17 @@ def gpu_identifier():
 
 # ---- oracle timing (CPU baseline and the reference arm) ------------------------------------
 
-def oracle_rate(edge_xy, nz, steps, budget=None):
-    """Time the FP64 oracle on a periodic slab edge_xy^2 x nz of the workload."""
+def oracle_rate(wl, nz, steps, budget=None):
+    """Time the FP64 oracle on a periodic slab of nz planes through the middle
+    of the workload wl (all of x and y)."""
     import oracle
-    from paper_2309_07801_gb300 import inputs
-    wl = inputs.translating_droplet(edge_xy)
-    rr, rb, u = inputs.workload_fields(wl)
     z0 = wl.nz // 2 - nz // 2
-    sl = slice(z0, z0 + nz)
+    rr, rb, u = workload_fields(wl, (z0, z0 + nz))
     p = wl.params()
     p["nz"] = nz
     d = oracle.Domain(oracle.make_params(**p))
-    d.init(np.ascontiguousarray(rr[sl]), np.ascontiguousarray(rb[sl]),
-           np.ascontiguousarray(u[:, sl]))
-    cells = edge_xy * edge_xy * nz
+    d.init(rr, rb, u)
+    cells = wl.nx * wl.ny * nz
     t0 = time.perf_counter()
     done = 0
     while done < steps:
@@ -241,14 +271,14 @@ def oracle_rate(edge_xy, nz, steps, budget=None):
     return cells * done / dt / 1e6, done, dt, cells
 
 
-def cpu_baseline(edge, budget):
+def cpu_baseline(wl, budget):
     import oracle
     oracle.build()
-    nz = max(1, min(edge, 16))
-    mlups, done, dt, cells = oracle_rate(edge, nz, 10 ** 6, budget)
+    nz = 4 if wl.nx >= 256 else max(1, min(wl.nz, 16))
+    mlups, done, dt, cells = oracle_rate(wl, nz, 10 ** 6, budget)
     return {"value": mlups, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": "%d steps of a %dx%dx%d periodic slab through the droplet of the %d^3 "
-                      "workload (FP64 oracle, %.1f s)" % (done, edge, edge, nz, edge, dt)}
+            "sample": "%d steps of a %dx%dx%d periodic slab through the middle of the %s workload "
+                      "(FP64 oracle, %.1f s)" % (done, wl.nx, wl.ny, nz, wl.name, dt)}
 
 
 def run_reference(args, dist):
@@ -256,14 +286,14 @@ def run_reference(args, dist):
         return
     import oracle
     oracle.build()
-    wl, _ = workload(args.edge)
+    wl = make_workload(args.workload, args.edge)
     # size the per-step slab so that warmup + steps fit in about two minutes
-    probe, _, _, _ = oracle_rate(args.edge, 1, 2)
+    probe, _, _, _ = oracle_rate(wl, 1, 2)
     budget_cells = probe * 1e6 * 120.0 / max(1, args.steps + args.warmup)
-    nz = int(max(1, min(args.edge, budget_cells // (args.edge * args.edge))))
+    nz = int(max(1, min(wl.nz, budget_cells // (wl.nx * wl.ny))))
     if args.warmup > 0:
-        oracle_rate(args.edge, nz, args.warmup)
-    mlups, done, dt, cells = oracle_rate(args.edge, nz, args.steps)
+        oracle_rate(wl, nz, args.warmup)
+    mlups, done, dt, cells = oracle_rate(wl, nz, args.steps)
     cores = oracle.threads()
     line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -271,9 +301,9 @@ def run_reference(args, dist):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": describe(wl), "cells": wl.cells, "parallelism": "cpu-oracle"},
             "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "each step: one step of a %dx%dx%d periodic slab of the "
-                                       "%d^3 workload (%d cells)" % (args.edge, args.edge, nz,
-                                                                     args.edge, cells)},
+                             "sample": "each step: one step of a %dx%dx%d periodic slab through the "
+                                       "middle of the %s workload (%d cells)"
+                                       % (wl.nx, wl.ny, nz, wl.name, cells)},
             "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -286,7 +316,8 @@ def run_ours(args, dist):
     if dist.world == 1:
         torch.cuda.set_device(0)
     build.build()
-    wl, (rr, rb, u) = workload(args.edge)
+    wl = make_workload(args.workload, args.edge)
+    rr, rb, u = workload_fields(wl)
     params = cg.make_params(precision="f32", **wl.params())
     N = wl.cells
     K, W = args.steps, max(3, args.warmup)
@@ -294,7 +325,9 @@ def run_ours(args, dist):
     d = cg.Domain(params)
     stream = d.stream
     d.init(rr, rb, u)
-    d.step(W)
+    # the first step builds the library's step graphs (both chain parities);
+    # at least two chains run before the timed region
+    d.step(max(W, 2 * GRAPH_STEPS + 1))
     torch.cuda.synchronize()
 
     clocks = ClockSampler(gpu_identifier())
@@ -313,50 +346,42 @@ def run_ours(args, dist):
     clk = clocks.stop()
     ms_total = dist.max(e0.elapsed_time(e1))
     mass, nonfinite = d.mass()
-    # the same K steps again with CUDA events around every pass (per-kernel
-    # device time for the roofline; kept out of the headline region)
-    cg.cg_profile_enable(d.h, K)
-    cg.cg_step(d.h, K)
+    # steps again with CUDA events around every pass (per-kernel device time
+    # for the roofline; plain launches, kept out of the headline region)
+    KP = max(1, min(K, 50))
+    cg.cg_profile_enable(d.h, KP)
+    cg.cg_step(d.h, KP)
     pass_ms, timed = cg.cg_profile_read(d.h)
     cg.cg_profile_enable(d.h, 0)
     value = N * K * dist.world / (ms_total * 1e-3) / 1e6
+    d.close()
+    del d
 
     peak, peak_kind = load_peaks()
-    collide_ms = pass_ms[cg.PASS_NAMES.index("k_collide")] / max(1, timed)
+    per_gpu = value / dist.world * 1e6
+    step_roofline = {"bound": "hbm", "peak": peak, "unit": "GB/s", "peak_kind": peak_kind,
+                     "paper_layout": {"bytes_per_cell": STEP_BYTES_432,
+                                      "achieved": per_gpu * STEP_BYTES_432 / 1e9,
+                                      "frac": per_gpu * STEP_BYTES_432 / (peak * 1e9)},
+                     "own_layout": {"bytes_per_cell": STATE_BYTES_248,
+                                    "achieved": per_gpu * STATE_BYTES_248 / 1e9,
+                                    "frac": per_gpu * STATE_BYTES_248 / (peak * 1e9)}}
+    pass_step_ms = {cg.PASS_NAMES[i]: pass_ms[i] / max(1, timed) for i in range(len(cg.PASS_NAMES))}
+    pass_frac = {k: PASS_BYTES[k] * N / (v * 1e-3) / 1e9 / peak for k, v in pass_step_ms.items()}
+    collide_ms = pass_step_ms["k_collide"]
     achieved = COLLIDE_BYTES_PER_CELL * N / (collide_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak,
                 "traffic": recorded_traffic("k_collide", N),
                 "peak_kind": peak_kind, "bytes_per_cell": COLLIDE_BYTES_PER_CELL,
-                "pass_ms_per_step": {cg.PASS_NAMES[i]: pass_ms[i] / max(1, timed)
-                                     for i in range(len(cg.PASS_NAMES))}}
-    step_roofline = {"bytes_per_cell": STEP_BYTES_432,
-                     "frac": value / dist.world * 1e6 * STEP_BYTES_432 / (peak * 1e9),
-                     "peak": peak, "unit": "GB/s"}
-    d.close()
+                "pass_ms_per_step": pass_step_ms, "pass_bytes_per_cell": PASS_BYTES,
+                "pass_frac": pass_frac,
+                "pass_timing": "plain launches, one pass after the other (%d steps)" % timed}
+    torch.cuda.empty_cache()
 
-    # end to end through the C ABI with pinned host buffers: upload the initial
-    # fields, advance K steps, read the macroscopic fields back
-    pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
-    h_rr, h_rb, h_u = pin(N), pin(N), pin(3 * N)
-    h_rr[:] = rr.reshape(-1)
-    h_rb[:] = rb.reshape(-1)
-    h_u[:] = u.reshape(-1)
-    o_rr, o_rb, o_u, o_p, o_phi = pin(N), pin(N), pin(3 * N), pin(N), pin(N)
-    d2 = cg.Domain(params)
-    d2.init(h_rr, h_rb, h_u)
-    d2.step(W)
-    torch.cuda.synchronize()
-    dist.barrier()
-    t0 = time.perf_counter()
-    cg.cg_init_fields(d2.h, h_rr, h_rb, h_u)
-    cg.cg_step(d2.h, K)
-    cg.cg_read_macros(d2.h, o_rr, o_rb, o_u, o_p, o_phi)
-    t_e2e = dist.max(time.perf_counter() - t0)
-    d2.close()
-    e2e = {"value": N * K * dist.world / t_e2e / 1e6, "unit": UNIT,
-           "h2d_bytes_per_step": 5 * 8 * N / K, "d2h_bytes_per_step": 7 * 8 * N / K,
-           "timed": "cg_init_fields (H2D) + cg_step(K) + cg_read_macros (D2H), host clock"}
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(params, (rr, rb, u), N, K, W, dist)
 
     if dist.rank != 0:
         return
@@ -367,48 +392,102 @@ def run_ours(args, dist):
                        "parallelism": "replicas" if dist.world > 1 else "single",
                        "l2": "inputs larger than L2: populations and recoloring state 2 x %.0f MB" %
                              (N * (27 + 6) * 4 / 1e6)},
-            "roofline": roofline, "step_roofline_432B": step_roofline,
+            "step_roofline": step_roofline, "roofline": roofline,
             "e2e": e2e, "gpu_launches": len(cg.PASS_NAMES) * K * step_slabs(wl.nz), "clocks": clk,
             "mass": list(map(float, mass)), "nonfinite": nonfinite}
+    single = None
     if not args.no_variants:
-        line["variants"] = variants(wl, (rr, rb, u), min(K, 800))
-        line["variants"]["f32_two_buffers"] = {"MLUPS": value / dist.world,
-                                              "workspace_bytes": cg.cg_workspace_bytes(params)}
+        line["variants"] = variants(wl, (rr, rb, u), value / dist.world, params, dist)
+        single = line["variants"].get("translating_droplet_128", {}).get("f32_two_buffers", {}).get("MLUPS")
+    del rr, rb, u
     if not args.no_serve:
-        line["serving"] = serving(args)
+        line["serving"] = serving(args, single)
     if not args.no_cpu_baseline and dist.world == 1:
-        line["cpu_baseline"] = cpu_baseline(args.edge, args.cpu_budget)
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_budget)
     elif not args.no_cpu_baseline:
         line["cpu_baseline"] = None
     print(json.dumps(line), flush=True)
 
 
-def variants(wl, fields, steps):
-    """The same workload in the other storage modes and with in-place
-    streaming: MLUPS (CUDA events around `steps` steps, best of two) and the
-    workspace each needs.  Accuracy of the 16-bit modes: tests/test_gpu_precision.py."""
+def end_to_end(params, fields, N, K, W, dist):
+    """The same K steps through the C ABI with pinned host buffers: upload the
+    initial fields, advance K steps, read the macroscopic fields back."""
     import torch
     from paper_2309_07801_gb300 import cg
-    out = {}
-    for prec, streaming in (("f32", 1), ("f16s", 0), ("f16s", 1), ("bf16s", 0), ("bf16s", 1)):
-        p = cg.make_params(precision=prec, streaming=streaming, **wl.params())
-        d = cg.Domain(p)
-        d.init(*fields)
-        d.step(16)
-        s = d.stream
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        best = float("inf")
-        for _ in range(2):
-            e0.record(s)
-            cg.cg_step(d.h, steps)
-            e1.record(s)
-            torch.cuda.synchronize()
-            best = min(best, e0.elapsed_time(e1))
-        mass, nonfinite = d.mass()
-        d.close()
-        out["%s_%s" % (prec, "in_place" if streaming else "two_buffers")] = {
-            "MLUPS": wl.cells * steps / (best * 1e-3) / 1e6, "workspace_bytes": cg.cg_workspace_bytes(p),
+    rr, rb, u = fields
+    pin = lambda n: torch.empty(n, dtype=torch.float64, pin_memory=True)
+    t_rr, t_rb, t_u = pin(N), pin(N), pin(3 * N)
+    h_rr, h_rb, h_u = t_rr.numpy(), t_rb.numpy(), t_u.numpy()
+    h_rr[:] = rr.reshape(-1)
+    h_rb[:] = rb.reshape(-1)
+    h_u[:] = u.reshape(-1)
+    outs = [pin(N), pin(N), pin(3 * N), pin(N), pin(N)]
+    o_rr, o_rb, o_u, o_p, o_phi = (t.numpy() for t in outs)
+    d2 = cg.Domain(params)
+    d2.init(h_rr, h_rb, h_u)
+    d2.step(max(W, 2 * GRAPH_STEPS + 1))
+    torch.cuda.synchronize()
+    dist.barrier()
+    t0 = time.perf_counter()
+    cg.cg_init_fields(d2.h, h_rr, h_rb, h_u)
+    cg.cg_step(d2.h, K)
+    cg.cg_read_macros(d2.h, o_rr, o_rb, o_u, o_p, o_phi)
+    t_e2e = dist.max(time.perf_counter() - t0)
+    d2.close()
+    del d2, t_rr, t_rb, t_u, outs
+    torch.cuda.empty_cache()
+    return {"value": N * K * dist.world / t_e2e / 1e6, "unit": UNIT,
+            "h2d_bytes_per_step": 5 * 8 * N / K, "d2h_bytes_per_step": 7 * 8 * N / K,
+            "timed": "cg_init_fields (H2D) + cg_step(K) + cg_read_macros (D2H), host clock"}
+
+
+def time_mode(wl, fields, prec, streaming, steps):
+    """MLUPS of one storage mode and layout (CUDA events around `steps` steps
+    after the graphs are built, best of two) and the workspace it needs."""
+    import torch
+    from paper_2309_07801_gb300 import cg
+    p = cg.make_params(precision=prec, streaming=streaming, **wl.params())
+    d = cg.Domain(p)
+    d.init(*fields)
+    d.step(2 * GRAPH_STEPS + 1)
+    s = d.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = float("inf")
+    for _ in range(2):
+        e0.record(s)
+        cg.cg_step(d.h, steps)
+        e1.record(s)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    mass, nonfinite = d.mass()
+    d.close()
+    del d
+    torch.cuda.empty_cache()
+    return {"MLUPS": wl.cells * steps / (best * 1e-3) / 1e6, "workspace_bytes": cg.cg_workspace_bytes(p),
             "nonfinite": nonfinite}
+
+
+def variants(wl, fields, value, params, dist):
+    """The headline workload in the 16-bit storage modes and with in-place
+    streaming, and the translating droplet at 128^3 in every mode (the
+    single-domain rate that the serving burst is compared with).  Accuracy of
+    the 16-bit modes: tests/test_gpu_precision.py."""
+    from paper_2309_07801_gb300 import cg, inputs
+    out = {}
+    head = {"f32_two_buffers": {"MLUPS": value, "workspace_bytes": cg.cg_workspace_bytes(params)}}
+    steps = max(40, min(800, int(2e8 / wl.cells)))
+    for prec, streaming in (("f32", 1), ("f16s", 1), ("bf16s", 1)):
+        head["%s_%s" % (prec, "in_place" if streaming else "two_buffers")] = \
+            time_mode(wl, fields, prec, streaming, steps)
+    out[wl.name] = head
+    if not wl.name.startswith("translating_droplet_128"):
+        tw = inputs.translating_droplet(128)
+        tf = inputs.workload_fields(tw)
+        row = {}
+        for prec, streaming in (("f32", 0), ("f32", 1), ("f16s", 0), ("f16s", 1), ("bf16s", 0), ("bf16s", 1)):
+            row["%s_%s" % (prec, "in_place" if streaming else "two_buffers")] = \
+                time_mode(tw, tf, prec, streaming, 800)
+        out[tw.name] = row
     return out
 
 
@@ -422,7 +501,7 @@ def _serve(mode, reqs):
                                 "max_active", "nonfinite_runs")}
 
 
-def serving(args):
+def serving(args, single_domain_mlups=None):
     """Continuous batching of independent runs (see paper_2309_07801_gb300/serve.py)."""
     from paper_2309_07801_gb300 import inputs
     warm = inputs.serving_requests(n=2, rate=1000.0, seed=5)
@@ -436,11 +515,12 @@ def serving(args):
                        (args.serve_requests, args.serve_rate),
            "cell_updates": int(sum(r.cells * r.steps for r in reqs)),
            "poisson": _serve("batched", reqs)}
-    if args.serve_compare:
+    if not args.no_serve_compare:
         burst = inputs.serving_requests(n=args.serve_requests, rate=1e9, seed=4)
         out["burst_batched"] = _serve("batched", burst)
         _serve("per_run", warm)
         out["burst_per_run"] = _serve("per_run", burst)
+        out["single_domain_128_f32_MLUPS"] = single_domain_mlups
     return out
 
 

@@ -168,8 +168,9 @@ int cg_init_fields(cg_ctx *ctx, const double *rho_r, const double *rho_b,
  * (asynchronous; returns after enqueueing).  A D3Q27 domain with nz >= 32 runs
  * as CUDA graphs of per-slab kernels (16-plane z slabs, the passes of
  * neighbouring slabs and of up to eight consecutive steps overlapping under
- * their data dependencies), built on first use per chain length and step
- * parity; while per-pass timing is on (cg_profile_enable) or the stream is
+ * their data dependencies); the first such call builds all of them (one
+ * step and an eight-step chain, for either parity of the first step), so
+ * later calls spend no host time on graph construction; while per-pass timing is on (cg_profile_enable) or the stream is
  * being captured by the caller, each pass is one plain launch instead.  The
  * results are the same either way, bit for bit.  CG_ERR_INVALID_ARG for a
  * negative count, a domain not initialised, or a member of a batch. */
@@ -228,7 +229,9 @@ int cg_profile_read(cg_ctx *ctx, double ms[CG_NUM_PASSES], int64_t *steps);
  * summation order).  The block partial sums live in a 64 KiB file-scope
  * __device__ array that every GPU loading the library holds until the process
  * exits.  The first call on a device looks up that array's device address
- * (make it before any stream capture).  Every call overwrites the slots it
+ * (make it before any stream capture) and keeps it for the process: after a
+ * cudaDeviceReset() of that device the kept address belongs to the destroyed
+ * context, so the process must not call this function again.  Every call overwrites the slots it
  * reads, so nothing has to start at zero, but all calls share the one array:
  * calls that overlap on the GPU (other streams, other host threads) race.
  * n above CG_NOALLOC_MAX_CELLS is rejected with CG_ERR_INVALID_ARG before any

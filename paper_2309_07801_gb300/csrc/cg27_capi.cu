@@ -302,10 +302,14 @@ int enqueue_steps(cg_ctx* c, int64_t remaining) {
   if (!ev && c->prm.nz >= 2 * SLAB_PLANES && c->slab_ok) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(c->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+      // all four graphs (one step and a chain, both parities) at the first
+      // use, so that no later call pays for an instantiation
+      for (int kk = 0; kk < 2; ++kk)
+        for (int par = 0; par < 2; ++par)
+          if (!c->sgraph[kk][par]) c->sgraph[kk][par] = build_slab_graph<T, SF, SOLID>(c, par, kk ? GRAPH_STEPS : 1);
       const int k = remaining >= GRAPH_STEPS ? 1 : 0;
       const int n = k ? GRAPH_STEPS : 1;
-      cudaGraphExec_t& gx = c->sgraph[k][cur];
-      if (!gx) gx = build_slab_graph<T, SF, SOLID>(c, cur, n);
+      cudaGraphExec_t gx = c->sgraph[k][cur];
       if (gx && cudaGraphLaunch(gx, c->stream) == cudaSuccess) return n;
       (void)cudaGetLastError();
       c->slab_ok = false;  // graphs unavailable here: plain launches from now on

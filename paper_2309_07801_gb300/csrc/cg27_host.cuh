@@ -60,7 +60,7 @@ struct cg_ctx {
   std::vector<cudaEvent_t> events;
   int64_t prof_capacity = 0, prof_used = 0;
   // graphs of the slab pipeline, [one step | a chain of steps][parity of the
-  // first step], built on first use
+  // first step], all four built by the first step that uses them
   cudaGraphExec_t sgraph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   bool slab_ok = true;
   ~cg_ctx() {

@@ -201,22 +201,29 @@ def droplet_collision(edge=512) -> Workload:
                     steps=10000, name="droplet_collision_%d" % edge)
 
 
-def collision_fields(wl: Workload):
-    """Two red droplets at x = c -+ 56/512 edge moving at +-0.1 along x."""
+def collision_fields(wl: Workload, z_range=None):
+    """Two red droplets at x = c -+ 56/512 edge moving at +-0.1 along x.
+    Filled plane by plane (a 512^3 domain needs no full-size temporaries);
+    z_range = (z0, z1) returns only those planes of the domain."""
     n = wl.nx
     R, d = 48.0 * n / 512.0, 56.0 * n / 512.0
-    shape = (wl.nz, wl.ny, wl.nx)
-    z, y, x = np.meshgrid(np.arange(wl.nz), np.arange(wl.ny), np.arange(wl.nx), indexing="ij")
+    z0, z1 = (0, wl.nz) if z_range is None else z_range
+    nzs = z1 - z0
     cx, cy, cz = n / 2.0, wl.ny / 2.0, wl.nz / 2.0
-    r1 = np.sqrt((x - (cx - d)) ** 2 + (y - cy) ** 2 + (z - cz) ** 2)
-    r2 = np.sqrt((x - (cx + d)) ** 2 + (y - cy) ** 2 + (z - cz) ** 2)
-    phi = np.maximum(np.tanh(2.0 * (R - r1) / 4.0), np.tanh(2.0 * (R - r2) / 4.0))
-    rho_r = wl.rho_r0 * (1.0 + phi) / 2.0
-    rho_b = wl.rho_b0 * (1.0 - phi) / 2.0
-    u = np.zeros((3,) + shape)
-    weight1 = (1.0 + np.tanh(2.0 * (R - r1) / 4.0)) / 2.0
-    weight2 = (1.0 + np.tanh(2.0 * (R - r2) / 4.0)) / 2.0
-    u[0] = 0.1 * weight1 - 0.1 * weight2
+    y, x = np.meshgrid(np.arange(wl.ny), np.arange(wl.nx), indexing="ij")
+    rho_r = np.empty((nzs, wl.ny, wl.nx))
+    rho_b = np.empty((nzs, wl.ny, wl.nx))
+    u = np.zeros((3, nzs, wl.ny, wl.nx))
+    for k in range(nzs):
+        z = z0 + k
+        r1 = np.sqrt((x - (cx - d)) ** 2 + (y - cy) ** 2 + (z - cz) ** 2)
+        r2 = np.sqrt((x - (cx + d)) ** 2 + (y - cy) ** 2 + (z - cz) ** 2)
+        t1 = np.tanh(2.0 * (R - r1) / 4.0)
+        t2 = np.tanh(2.0 * (R - r2) / 4.0)
+        phi = np.maximum(t1, t2)
+        rho_r[k] = wl.rho_r0 * (1.0 + phi) / 2.0
+        rho_b[k] = wl.rho_b0 * (1.0 - phi) / 2.0
+        u[0, k] = 0.1 * ((1.0 + t1) / 2.0) - 0.1 * ((1.0 + t2) / 2.0)
     return rho_r, rho_b, u
 
 

@@ -222,6 +222,96 @@ def test_f32_translating_droplet_128_full_size():
     assert m["u_abs"] <= 1e-6, m
 
 
+# The schedule the benchmark runs: 8-step chained slab graphs.  Steps 0-7 form
+# one chain starting at an even step, step 8 is a single-step graph, steps
+# 9-16 and 17-24 are chains starting at odd steps.
+BENCH_SCHEDULE = (8, 1, 8, 8)
+
+
+def _run_schedule(dom, schedule=BENCH_SCHEDULE):
+    for k in schedule:
+        dom.step(k)
+
+
+def test_f32_128_vs_oracle_through_chained_slab_graphs():
+    """128^3 (eight 16-plane slabs) in FP32 against the oracle after 25 steps
+    that run as eight-step chains of both parities, on every cell."""
+    import oracle
+    from paper_2309_07801_gb300 import cg
+    wl = inputs.translating_droplet(128)
+    rr, rb, u = inputs.workload_fields(wl)
+    od = oracle.Domain(oracle.make_params(**wl.params()))
+    od.init(rr, rb, u)
+    od.step(sum(BENCH_SCHEDULE))
+    gd = cg.Domain(cg.make_params(precision="f32", **wl.params()))
+    gd.init(rr, rb, u)
+    _run_schedule(gd)
+    assert gd.steps == sum(BENCH_SCHEDULE)
+    m = compare_macros(od, gd)
+    assert m["rho_cellrel"] <= 1e-5, m
+    assert m["u_abs"] <= 1e-6, m
+
+
+def test_f32_512_collision_equals_its_tiled_128_copy():
+    """The benchmark's domain (512^3 head-on collision parameters, FP32, two
+    buffers, 32 slabs, chained graphs of both parities) started from the 128^3
+    collision fields tiled 4 x 4 x 4: by periodicity every 128^3 tile must
+    evolve exactly as the 128^3 domain does, which is checked against the
+    oracle.  Equality is bitwise, cell by cell, over the whole 512^3 domain."""
+    import oracle
+    from paper_2309_07801_gb300 import cg
+    small = inputs.droplet_collision(128)
+    rr, rb, u = inputs.collision_fields(small)
+    steps = sum(BENCH_SCHEDULE)
+    od = oracle.Domain(oracle.make_params(**small.params()))
+    od.init(rr, rb, u)
+    od.step(steps)
+    gs = cg.Domain(cg.make_params(precision="f32", **small.params()))
+    gs.init(rr, rb, u)
+    _run_schedule(gs)
+    m = compare_macros(od, gs)
+    assert m["rho_cellrel"] <= 1e-5, m
+    assert m["u_abs"] <= 1e-6, m
+    ref = gs.macros()
+    gs.close()
+    od.close()
+    big = inputs.droplet_collision(512)
+    p = big.params()
+    gb = cg.Domain(cg.make_params(precision="f32", **p))
+    gb.init(np.tile(rr, (4, 4, 4)), np.tile(rb, (4, 4, 4)), np.tile(u, (1, 4, 4, 4)))
+    del rr, rb, u
+    _run_schedule(gb)
+    mass, flag = gb.mass()
+    assert flag == 0
+    got = gb.macros()
+    gb.close()
+    for key in ("rho_r", "rho_b", "p", "phi"):
+        assert np.array_equal(got[key], np.tile(ref[key], (4, 4, 4))), key
+    assert np.array_equal(got["u"], np.tile(ref["u"], (1, 4, 4, 4)))
+
+
+def test_f16s_128_vs_f32_through_chained_slab_graphs():
+    """The 128^3 translating droplet stored as FP16 deviations, 201 steps
+    through chained slab graphs of both parities, against the FP32 run (which
+    is within 1e-5 of the oracle): within the bars that the 32^3 copy of this
+    workload meets against the oracle (density 3e-3 per cell, |du| 2e-4)."""
+    from paper_2309_07801_gb300 import cg
+    wl = inputs.translating_droplet(128)
+    fields = inputs.workload_fields(wl)
+    out = {}
+    for prec in ("f32", "f16s"):
+        d = cg.Domain(cg.make_params(precision=prec, **wl.params()))
+        d.init(*fields)
+        _run_schedule(d, (8, 1) + (8,) * 24)
+        assert d.mass()[1] == 0
+        out[prec] = d.macros()
+        d.close()
+    a, b = out["f16s"], out["f32"]
+    rho_a, rho_b = a["rho_r"] + a["rho_b"], b["rho_r"] + b["rho_b"]
+    assert np.max(np.abs(rho_a - rho_b) / rho_b) <= 3e-3
+    assert np.max(np.abs(a["u"] - b["u"])) <= 2e-4
+
+
 def test_f32_full_size_conservation_and_translation():
     """At full size: per-colour mass conserved over 100 steps, and a periodic
     shift of the input shifts the output bit for bit."""
@@ -305,10 +395,12 @@ def test_invalid_inputs_rejected_before_launch():
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16s"])
-def test_slab_graph_schedule_is_bitwise_equal_to_plain_launches(prec):
-    """Domains with nz >= 48 step through the slab-pipeline graphs (single steps
-    and chains of eight, both parities); with per-pass timing on, the same steps
-    run as plain launches.  Same results."""
+@pytest.mark.parametrize("first", [3, 4])
+def test_slab_graph_schedule_is_bitwise_equal_to_plain_launches(prec, first):
+    """Domains with nz >= 32 step through the slab-pipeline graphs (single steps
+    and chains of eight); with per-pass timing on, the same steps run as plain
+    launches.  Same results.  `first` single steps come before the chains, so
+    the chains start at an odd (3) or an even (4) step: both parities."""
     from paper_2309_07801_gb300 import cg
     wl = inputs.translating_droplet(64)
     fields = inputs.workload_fields(wl, noise=1e-3, seed=3)
@@ -318,8 +410,8 @@ def test_slab_graph_schedule_is_bitwise_equal_to_plain_launches(prec):
         d.init(*fields)
         if profile:
             cg.cg_profile_enable(d.h, 40)
-        d.step(3)
-        d.step(37)
+        d.step(first)
+        d.step(40 - first)
         out.append(d.macros())
         d.close()
     for key in out[0]:

@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define CG27_ABI_VERSION 3
+#define CG27_ABI_VERSION 4
 
 /* return codes */
 #define CG_OK 0
@@ -194,6 +194,47 @@ int cg_read_populations(cg_ctx *ctx, double *fr, double *fb);
  * step since cg_init_fields() produced a non-finite density, else 0.  Either
  * pointer may be NULL. */
 int cg_reduce(cg_ctx *ctx, double out_mass[2], int32_t *nonfinite);
+
+/* Diagnostics of the latest state (the fields cg_read_macros() reports),
+ * reduced on the device in FP64 in a fixed order (bitwise reproducible; no
+ * field is read back to the host).  Cell (x, y, z) sits at coordinates
+ * (x, y, z).  They are the quantities of the paper's tests:
+ *   mass[k]            sum of rho_k over all cells (k = 0 red, 1 blue);
+ *   red_volume         sum of (1 + phi)/2 over fluid cells (Eq. order
+ *                      parameter; the droplet volume of the Laplace test);
+ *   momentum[k][a]     sum of rho_k u_a over fluid cells (u includes F/2);
+ *                      momentum[1][2] / mass[1] is the bubble velocity V_c of
+ *                      Sec. IV.D when no solid cell holds blue mass;
+ *   centroid[k][a]     rho_k-weighted centroid: the circular mean
+ *                      (n/2pi) atan2(sum rho_k sin(2pi x/n), sum rho_k cos(2pi x/n))
+ *                      in [0, n) along a periodic axis, sum rho_k x / sum rho_k
+ *                      along a wall axis (the bubble height z_c of Sec. IV.D);
+ *   second_moment[6]   sum rho_r d_a d_b / sum rho_r about the red centroid
+ *                      (xx, yy, zz, xy, xz, yz), d the minimum-image offset
+ *                      along periodic axes (droplet shape, Sec. IV.B);
+ *   p_in, p_out        mean pressure (Eq. pressure) over fluid cells with
+ *                      |x - center| < r_in and > r_out (minimum image along
+ *                      periodic axes; NaN where no cell qualifies), n_in,
+ *                      n_out the cell counts: p_in - p_out is the pressure
+ *                      jump of the Laplace test (Sec. IV.A);
+ *   u_max              largest |u| over fluid cells;
+ *   nonfinite          as in cg_reduce().
+ * center may be NULL (the origin); r_out may be +infinity (no outer cells).
+ * Synchronises the domain's stream.  The scratch lives in the workspace. */
+typedef struct cg_diagnostics {
+  double mass[2];
+  double red_volume;
+  double momentum[2][3];
+  double centroid[2][3];
+  double second_moment[6];
+  double p_in, p_out;
+  int64_t n_in, n_out;
+  double u_max;
+  int32_t nonfinite;
+  int32_t reserved;
+} cg_diagnostics;
+int cg_reduce_diagnostics(cg_ctx *ctx, const double center[3], double r_in,
+                          double r_out, cg_diagnostics *out);
 
 /* Checkpoint: cg_state_bytes() gives the size of an opaque host blob that
  * cg_save_state() fills and cg_load_state() restores into a domain created

@@ -48,6 +48,14 @@ class cg_params(ctypes.Structure):
                 ("streaming", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
+class cg_diagnostics(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double * 2), ("red_volume", ctypes.c_double),
+                ("momentum", (ctypes.c_double * 3) * 2), ("centroid", (ctypes.c_double * 3) * 2),
+                ("second_moment", ctypes.c_double * 6), ("p_in", ctypes.c_double),
+                ("p_out", ctypes.c_double), ("n_in", ctypes.c_int64), ("n_out", ctypes.c_int64),
+                ("u_max", ctypes.c_double), ("nonfinite", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 # exported entry points of include/cg27.h: name -> (restype, argtypes)
 _VP, _DP = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
 SIGNATURES = {
@@ -61,6 +69,8 @@ SIGNATURES = {
     "cg_read_macros": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "cg_read_populations": (ctypes.c_int, [_VP, _VP, _VP]),
     "cg_reduce": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_int32)]),
+    "cg_reduce_diagnostics": (ctypes.c_int, [_VP, _VP, ctypes.c_double, ctypes.c_double,
+                                             ctypes.POINTER(cg_diagnostics)]),
     "cg_state_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
     "cg_save_state": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "cg_load_state": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
@@ -163,6 +173,19 @@ def cg_reduce(h):
     flag = ctypes.c_int32(0)
     _check(lib().cg_reduce(h, _ptr(m), ctypes.byref(flag)))
     return m, int(flag.value)
+
+
+def cg_reduce_diagnostics(h, center=(0.0, 0.0, 0.0), r_in=0.0, r_out=float("inf")) -> dict:
+    """Device-side FP64 diagnostics of the latest state (see the C header)."""
+    c = np.ascontiguousarray(center, dtype=np.float64)
+    out = cg_diagnostics()
+    _check(lib().cg_reduce_diagnostics(h, _ptr(c), float(r_in), float(r_out), ctypes.byref(out)))
+    return {"mass": np.array(out.mass[:]), "red_volume": out.red_volume,
+            "momentum": np.array([out.momentum[k][:] for k in range(2)]),
+            "centroid": np.array([out.centroid[k][:] for k in range(2)]),
+            "second_moment": np.array(out.second_moment[:]), "p_in": out.p_in, "p_out": out.p_out,
+            "n_in": int(out.n_in), "n_out": int(out.n_out), "u_max": out.u_max,
+            "nonfinite": int(out.nonfinite)}
 
 
 def cg_state_bytes(h) -> int:
@@ -298,6 +321,9 @@ class Domain:
 
     def mass(self):
         return cg_reduce(self.h)
+
+    def diagnostics(self, center=(0.0, 0.0, 0.0), r_in=0.0, r_out=float("inf")) -> dict:
+        return cg_reduce_diagnostics(self.h, center, r_in, r_out)
 
     def save(self) -> np.ndarray:
         buf = np.empty(cg_state_bytes(self.h), dtype=np.uint8)

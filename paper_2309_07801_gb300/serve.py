@@ -1,7 +1,8 @@
 """Continuous-batching server for many independent colour-gradient runs.
 
 Requests (a droplet problem, a step count, an arrival time) are admitted while
-device memory and batch slots allow; every admitted run keeps its state on the
+the device's free memory (as the driver reports it at admission time) and the
+batch slots allow; every admitted run keeps its state on the
 device and all active runs advance together.  In the "batched" mode one batch
 step is four shared launches over the tiles of every active run (cg_batch_*,
 replayed from CUDA graphs); in the "per_run" mode each run is stepped with its
@@ -89,12 +90,16 @@ ADMIT_SLICE = 0.02  # seconds of admission work before a quantum (batched mode)
 
 class Server:
     """mode: "batched" (shared launches) or "per_run" (one run's launches at a
-    time).  hbm_budget: bytes of workspace the active runs may hold (default:
-    80 % of the device memory); max_active: batch slots; quantum: most steps
+    time).  A request is admitted when its workspace fits the device memory
+    that is free at that moment (cudaMemGetInfo, plus what PyTorch's caching
+    allocator holds unused) less a reserve of `reserve` bytes (default: 2 %
+    of the device memory), and, if hbm_budget is given, when the active runs'
+    workspaces stay within it; max_active: batch slots; quantum: most steps
     advanced between admission checks."""
 
     def __init__(self, mode="batched", precision="f32", max_active=256, quantum=100,
-                 hbm_budget: Optional[int] = None, device="cuda", keep_macros=False, depth=0):
+                 hbm_budget: Optional[int] = None, device="cuda", keep_macros=False, depth=0,
+                 reserve: Optional[int] = None):
         import torch
         if mode not in ("batched", "per_run"):
             raise ValueError("mode must be 'batched' or 'per_run'")
@@ -102,7 +107,9 @@ class Server:
         self.max_active, self.keep_macros = int(max_active), keep_macros
         self.device = torch.device(device)
         total = torch.cuda.get_device_properties(self.device).total_memory
-        self.hbm_budget = int(0.8 * total) if hbm_budget is None else int(hbm_budget)
+        self.total_memory = total
+        self.hbm_budget = None if hbm_budget is None else int(hbm_budget)
+        self.reserve = int(0.02 * total) if reserve is None else int(reserve)
         self.stream = torch.cuda.Stream(self.device)
         # initialisation of the runs of a batch, beside the batch's steps
         self.io_stream = torch.cuda.Stream(self.device)
@@ -112,6 +119,15 @@ class Server:
             if depth:
                 self.batch.set_depth(depth)
         self.log: List[tuple] = []
+
+    def free_bytes(self) -> int:
+        """Device memory a new workspace can take now: free memory as the
+        driver reports it plus blocks PyTorch's allocator caches unused, less
+        the reserve."""
+        import torch
+        free, _ = torch.cuda.mem_get_info(self.device)
+        cached = torch.cuda.memory_reserved(self.device) - torch.cuda.memory_allocated(self.device)
+        return free + cached - self.reserve
 
     def close(self):
         if self.batch is not None:
@@ -148,10 +164,19 @@ class Server:
                     len(active) + len(joining) < self.max_active and go_on(n):
                 need = cg.cg_workspace_bytes(cg.make_params(precision=self.precision,
                                                             **pending[i].workload().params()))
-                if need > self.hbm_budget:
-                    raise ValueError("request %d needs %d bytes of workspace, more than the budget of %d"
-                                     % (pending[i].rid, need, self.hbm_budget))
-                if used + need > self.hbm_budget:
+                cap = self.total_memory - self.reserve
+                if self.hbm_budget is not None:
+                    cap = min(cap, self.hbm_budget)
+                if need > cap:
+                    raise ValueError("request %d needs %d bytes of workspace, more than the %d this device "
+                                     "can give a run" % (pending[i].rid, need, cap))
+                if self.hbm_budget is not None and used + need > self.hbm_budget:
+                    break
+                if need > self.free_bytes():
+                    if not active and not joining:
+                        raise RuntimeError("request %d needs %d bytes of workspace and the device has only "
+                                           "%d free with no run active" % (pending[i].rid, need,
+                                                                           self.free_bytes()))
                     break
                 joining.append(self._admit(pending[i], clock() - t0))
                 used += need

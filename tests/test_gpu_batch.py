@@ -276,3 +276,20 @@ def test_server_admission_respects_the_memory_budget():
     res = srv.run(reqs)
     srv.close()
     assert res["runs"] == len(reqs) and res["max_active"] == 1
+
+
+def test_server_admission_follows_free_device_memory():
+    """Without a fixed budget a request is admitted only while the device's
+    free memory (less the reserve) holds its workspace: with the reserve set
+    so that one and a half workspaces are free, the runs go one at a time."""
+    from paper_2309_07801_gb300 import cg, serve
+    reqs = _requests(n=4, seed=12)
+    for r in reqs:  # one size, so that one and a half workspaces hold exactly one run
+        r.edge, r.radius = 48, 0.3 * 48
+    one = max(cg.cg_workspace_bytes(cg.make_params(precision="f32", **r.workload().params())) for r in reqs)
+    srv = serve.Server(mode="batched", quantum=20)
+    srv.reserve += srv.free_bytes() - int(1.5 * one)
+    assert one <= srv.free_bytes() < 2 * one
+    res = srv.run(reqs)
+    srv.close()
+    assert res["runs"] == len(reqs) and res["max_active"] == 1 and res["nonfinite_runs"] == 0

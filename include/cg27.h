@@ -168,13 +168,33 @@ int cg_init_fields(cg_ctx *ctx, const double *rho_r, const double *rho_b,
  * (asynchronous; returns after enqueueing).  A D3Q27 domain with nz >= 32 runs
  * as CUDA graphs of per-slab kernels (16-plane z slabs, the passes of
  * neighbouring slabs and of up to eight consecutive steps overlapping under
- * their data dependencies); the first such call builds all of them (one
- * step and an eight-step chain, for either parity of the first step), so
- * later calls spend no host time on graph construction; while per-pass timing is on (cg_profile_enable) or the stream is
+ * their data dependencies; see cg_set_schedule below); the first call with a
+ * schedule builds all of its graphs (one step and an eight-step chain, for
+ * either parity of the first step), so later calls spend no host time on
+ * graph construction; while per-pass timing is on (cg_profile_enable) or the stream is
  * being captured by the caller, each pass is one plain launch instead.  The
  * results are the same either way, bit for bit.  CG_ERR_INVALID_ARG for a
  * negative count, a domain not initialised, or a member of a batch. */
 int cg_step(cg_ctx *ctx, int64_t nsteps);
+
+/* Schedule of the step graphs (D3Q27 domains with nz >= 32).  The z range is
+ * cut into slabs of `planes` planes; each pass of each slab is one kernel
+ * whose tiles march `tz` planes, and the passes of neighbouring slabs and of
+ * up to eight steps overlap under their data dependencies (planes = nz: one
+ * kernel per pass over the whole domain).  Thin slabs overlap more but repeat
+ * the z halo of the stencil passes at every tile start.  Unless the caller
+ * fixes it, the schedule is chosen by the library's tuner: the first chained
+ * steps of the domain time the candidates -- 16/8, 32/16 and 64/32 planes per
+ * slab / per tile where the domain holds two such slabs, and the whole domain
+ * at the default depth -- one untimed and two timed eight-step chains each,
+ * waiting for the GPU after each candidate, and keep the fastest.  These are
+ * ordinary steps: results do not depend on the schedule, bit for bit.
+ * cg_set_schedule(ctx, planes, tz) fixes it (1 <= planes <= nz,
+ * 1 <= tz <= planes), cg_set_schedule(ctx, 0, 0) starts tuning again; both
+ * wait for the domain's stream.  cg_schedule() reports the schedule in use
+ * (0, 0 before the first graph step) and whether tuning is under way. */
+int cg_set_schedule(cg_ctx *ctx, int32_t planes, int32_t tz);
+int cg_schedule(cg_ctx *ctx, int32_t *planes, int32_t *tz, int32_t *tuning);
 
 /* Copy the fields of the latest post-streaming state to host arrays (each may
  * be NULL): rho_r[N], rho_b[N], u[3N] (Eq. for rho u, including F/2), p[N]

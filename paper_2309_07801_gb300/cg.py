@@ -75,6 +75,9 @@ SIGNATURES = {
     "cg_save_state": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "cg_load_state": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "cg_steps_taken": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
+    "cg_set_schedule": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
+    "cg_schedule": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                   ctypes.POINTER(ctypes.c_int32)]),
     "cg_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "cg_profile_read": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_int64)]),
     "cg_mass_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_int32, _VP, _VP]),
@@ -208,6 +211,17 @@ def cg_steps_taken(h) -> int:
     return n.value
 
 
+def cg_set_schedule(h, planes: int, tz: int):
+    _check(lib().cg_set_schedule(h, int(planes), int(tz)))
+
+
+def cg_schedule(h):
+    """(planes, tz, tuning) of the step graphs."""
+    a, b, t = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(lib().cg_schedule(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(t)))
+    return a.value, b.value, bool(t.value)
+
+
 def cg_profile_enable(h, max_steps: int):
     _check(lib().cg_profile_enable(h, int(max_steps)))
 
@@ -336,6 +350,24 @@ class Domain:
     @property
     def steps(self) -> int:
         return cg_steps_taken(self.h)
+
+    @property
+    def schedule(self):
+        return cg_schedule(self.h)
+
+    def set_schedule(self, planes: int, tz: int):
+        cg_set_schedule(self.h, planes, tz)
+
+    def tune(self, max_steps: int = 400) -> int:
+        """Step until the schedule tuner has chosen (at most max_steps steps);
+        returns the steps taken."""
+        n = 0
+        self.step(1)
+        n += 1
+        while self.schedule[2] and n < max_steps:
+            self.step(8)
+            n += 8
+        return n
 
 
 # ---- batches --------------------------------------------------------------------------------

@@ -149,13 +149,58 @@ dim3 grid_of(const cg_params& p, dim3 b) {
   return dim3((p.nx + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, p.nz);
 }
 
-// z slabs of the step graphs: SLAB_PLANES planes in chunks of SLAB_TZ per tile
-// (16 and 8 measured best at 128^3 on GB300, with eight-step chains, among
-// 16/24/32/48 planes and 4/8/12/16 per tile)
-constexpr int SLAB_PLANES = 16, SLAB_TZ = 8;
-// steps chained in one slab graph (8: +6 % over one step per graph at 128^3,
+// The step graphs cut the domain into z slabs of `planes` planes whose tiles
+// march `tz` planes (the schedule).  Thin slabs let the passes of
+// neighbouring slabs overlap but repeat the z halo of the stencil passes at
+// every tile start; thick ones do the opposite.  16 planes in tiles of 8
+// measured best at 128^3 (among 16/24/32/48 planes and 4/8/12/16 per tile);
+// at 512^3 the kernels fill the GPU on their own and the halo repeats cost
+// more than the overlap gains.  So the first chained steps of a domain time
+// the candidates below and keep the fastest (results do not depend on the
+// schedule).  Graphs are used from SLAB_MIN_NZ planes on.
+constexpr int SLAB_MIN_NZ = 32;
+// steps chained in one graph (8: +6 % over one step per graph at 128^3,
 // 16 gains 0.3 % more)
 constexpr int GRAPH_STEPS = 8;
+// chains of each candidate: one untimed, then TUNE_CHAINS timed
+constexpr int TUNE_CHAINS = 2;
+
+// candidate schedules (planes, tz) of a domain with nz >= SLAB_MIN_NZ: thin
+// slabs where the domain holds at least two, and whole-domain kernels with the
+// domain's default depth
+std::vector<std::pair<int, int>> schedule_candidates(const cg_ctx* c) {
+  std::vector<std::pair<int, int>> v;
+  const int nz = c->prm.nz;
+  for (auto pt : {std::make_pair(16, 8), std::make_pair(32, 16), std::make_pair(64, 32)})
+    if (nz >= 2 * pt.first) v.push_back(pt);
+  v.push_back({nz, std::min(c->tz, nz)});
+  return v;
+}
+
+void drop_graphs(cg_ctx* c) {
+  for (auto& row : c->sgraph)
+    for (cudaGraphExec_t& g : row)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+}
+
+// switch the graph path to schedule (planes, tz); its graphs are built at the next step
+void set_schedule(cg_ctx* c, int planes, int tz) {
+  if (c->sched_planes != planes || c->sched_tz != tz) drop_graphs(c);
+  c->sched_planes = planes;
+  c->sched_tz = tz;
+}
+
+// (re)start tuning: the candidates are timed by the next chained steps
+void start_tuning(cg_ctx* c) {
+  c->sched_cand = schedule_candidates(c);
+  c->sched_timed.clear();
+  c->tune_phase = 0;
+  set_schedule(c, c->sched_cand.front().first, c->sched_cand.front().second);
+  if (c->sched_cand.size() == 1) c->sched_cand.clear();  // nothing to choose
+}
 
 // the macroscopic pass and the collision of a step of stream mode sm
 template <typename T, typename SF, bool SOLID>
@@ -218,7 +263,7 @@ void launch_passes(cg_ctx* c, int cur, cudaEvent_t* ev, int zb, int ze) {
 // the previous one.  Results do not depend on the slabs or the chaining.
 template <typename T, typename SF, bool SOLID>
 cudaGraphExec_t build_slab_graph(cg_ctx* c, int cur0, int nsteps) {
-  const int slab = SLAB_PLANES;
+  const int slab = c->sched_planes;
   const int nz = c->prm.nz, ns = (nz + slab - 1) / slab;
   const Geom g = make_geom(c);
   const Ptrs<T> P[2] = {make_ptrs<T>(c, 0), make_ptrs<T>(c, 1)};
@@ -241,7 +286,7 @@ cudaGraphExec_t build_slab_graph(cg_ctx* c, int cur0, int nsteps) {
   for (int i = 0; i < ns; ++i) {
     zb[i] = i * slab;
     ze[i] = std::min(nz, zb[i] + slab);
-    tzs[i] = std::min(SLAB_TZ, ze[i] - zb[i]);
+    tzs[i] = std::min(c->sched_tz, ze[i] - zb[i]);
   }
   auto add = [&](cudaGraphNode_t* node, void* func, dim3 gr, dim3 blk, void** args,
                  const std::vector<cudaGraphNode_t>& dv) {
@@ -292,28 +337,63 @@ cudaGraphExec_t build_slab_graph(cg_ctx* c, int cur0, int nsteps) {
   return ex;
 }
 
+// One step of the tuning of the schedule when a chain is launched: an untimed
+// chain of the current candidate, then TUNE_CHAINS chains between two events
+// (waiting for them); after the last candidate the fastest is kept.
+// Returns false when the chain could not be launched.
+bool launch_chain_tuned(cg_ctx* c, cudaGraphExec_t gx) {
+  if (c->sched_cand.empty()) return cudaGraphLaunch(gx, c->stream) == cudaSuccess;
+  if (!c->tev[0]) {
+    if (cudaEventCreate(&c->tev[0]) != cudaSuccess || cudaEventCreate(&c->tev[1]) != cudaSuccess) return false;
+  }
+  if (c->tune_phase == 1) cudaEventRecord(c->tev[0], c->stream);
+  if (cudaGraphLaunch(gx, c->stream) != cudaSuccess) return false;
+  if (c->tune_phase == 0) {
+    c->tune_phase = 1;
+    return true;
+  }
+  if (++c->tune_phase <= TUNE_CHAINS) return true;  // more chains of this candidate
+  cudaEventRecord(c->tev[1], c->stream);
+  if (cudaEventSynchronize(c->tev[1]) != cudaSuccess) return false;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->tev[0], c->tev[1]);
+  c->sched_timed.push_back({ms, c->sched_cand.front()});
+  c->sched_cand.erase(c->sched_cand.begin());
+  c->tune_phase = 0;
+  if (!c->sched_cand.empty()) {
+    set_schedule(c, c->sched_cand.front().first, c->sched_cand.front().second);
+  } else {
+    const auto best = std::min_element(c->sched_timed.begin(), c->sched_timed.end());
+    set_schedule(c, best->second.first, best->second.second);
+  }
+  return true;
+}
+
 // Enqueues up to `remaining` steps (at least one) and returns how many.
 template <typename T, typename SF, bool SOLID>
 int enqueue_steps(cg_ctx* c, int64_t remaining) {
   const int cur = (int)(c->steps & 1);
   cudaEvent_t* ev = nullptr;
   if (c->prof_used < c->prof_capacity) ev = &c->events[NUM_EVENTS_PER_STEP * c->prof_used++];
-  // the slab graphs when the domain has at least two slabs, no per-pass
-  // timing is requested and the stream is not being captured by the caller
-  if (!ev && c->prm.nz >= 2 * SLAB_PLANES && c->slab_ok) {
+  // the step graphs when the domain has at least SLAB_MIN_NZ planes, no
+  // per-pass timing is requested and the stream is not being captured
+  if (!ev && c->prm.nz >= SLAB_MIN_NZ && c->graphs_ok) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(c->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
-      // all four graphs (one step and a chain, both parities) at the first
-      // use, so that no later call pays for an instantiation
+      if (c->sched_planes == 0) start_tuning(c);
+      // all four graphs of the schedule (one step and a chain, both parities)
+      // at its first use, so that no later call pays for an instantiation
       for (int kk = 0; kk < 2; ++kk)
         for (int par = 0; par < 2; ++par)
           if (!c->sgraph[kk][par]) c->sgraph[kk][par] = build_slab_graph<T, SF, SOLID>(c, par, kk ? GRAPH_STEPS : 1);
       const int k = remaining >= GRAPH_STEPS ? 1 : 0;
       const int n = k ? GRAPH_STEPS : 1;
+      // a single step inside a timed window would falsify it: time again
+      if (!k && !c->sched_cand.empty() && c->tune_phase > 1) c->tune_phase = 1;
       cudaGraphExec_t gx = c->sgraph[k][cur];
-      if (gx && cudaGraphLaunch(gx, c->stream) == cudaSuccess) return n;
+      if (gx && (k ? launch_chain_tuned(c, gx) : cudaGraphLaunch(gx, c->stream) == cudaSuccess)) return n;
       (void)cudaGetLastError();
-      c->slab_ok = false;  // graphs unavailable here: plain launches from now on
+      c->graphs_ok = false;  // graphs unavailable here: plain launches from now on
     }
   }
   launch_passes<T, SF, SOLID>(c, cur, ev, 0, c->prm.nz);
@@ -789,6 +869,34 @@ int cg_profile_read(cg_ctx* c, double ms[CG_NUM_PASSES], int64_t* steps) {
   if (ms)
     for (int k = 0; k < CG_NUM_PASSES; ++k) ms[k] = acc[k];
   if (steps) *steps = c->prof_used;
+  return CG_OK;
+}
+
+int cg_set_schedule(cg_ctx* c, int32_t planes, int32_t tz) {
+  if (!c) return fail(CG_ERR_INVALID_ARG, "ctx is NULL");
+  if (c->batch) return fail(CG_ERR_INVALID_ARG, "the domain is a member of a batch: remove it first");
+  if (planes == 0 && tz == 0) {
+    CG_CUDA(cudaStreamSynchronize(c->stream));  // graphs of the old schedule may be in flight
+    c->sched_planes = 0;  // tune again at the next graph step
+    drop_graphs(c);
+    return CG_OK;
+  }
+  if (planes < 1 || planes > c->prm.nz || tz < 1 || tz > planes)
+    return fail(CG_ERR_INVALID_ARG, "need 1 <= planes <= nz and 1 <= tz <= planes (or both 0)");
+  CG_CUDA(cudaStreamSynchronize(c->stream));  // graphs of the old schedule may be in flight
+  c->sched_cand.clear();
+  c->sched_timed.clear();
+  set_schedule(c, planes, tz);
+  return CG_OK;
+}
+
+int cg_schedule(cg_ctx* c, int32_t* planes, int32_t* tz, int32_t* tuning) {
+  if (!c) return fail(CG_ERR_INVALID_ARG, "ctx is NULL");
+  if (planes) *planes = c->sched_planes;
+  if (tz) *tz = c->sched_tz;
+  if (tuning)
+    *tuning = c->graphs_ok && c->prm.lattice == CG_D3Q27 &&
+              ((c->sched_planes == 0 && c->prm.nz >= SLAB_MIN_NZ) || !c->sched_cand.empty());
   return CG_OK;
 }
 

@@ -69,9 +69,18 @@ struct cg_ctx {
   // graphs of the slab pipeline, [one step | a chain of steps][parity of the
   // first step], all four built by the first step that uses them
   cudaGraphExec_t sgraph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-  bool slab_ok = true;
+  bool graphs_ok = true;
+  // schedule of the graphs: slabs of sched_planes planes, tiles of sched_tz
+  // planes (0: not chosen yet); candidates still to time and the timings
+  int sched_planes = 0, sched_tz = 0;
+  std::vector<std::pair<int, int>> sched_cand;
+  std::vector<std::pair<float, std::pair<int, int>>> sched_timed;
+  int tune_phase = 0;  // 0: next chain untimed, 1..: timed chains of the candidate
+  cudaEvent_t tev[2] = {nullptr, nullptr};
   ~cg_ctx() {
     for (cudaEvent_t e : events) cudaEventDestroy(e);
+    for (cudaEvent_t e : tev)
+      if (e) cudaEventDestroy(e);
     for (auto& row : sgraph)
       for (cudaGraphExec_t g : row)
         if (g) cudaGraphExecDestroy(g);

@@ -966,7 +966,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !SOLID) ? 4 : 1)
 }
 
 template <typename T, bool SOLID, bool PERSIST>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, (!SOLID && sizeof(T) == 4) ? 3 : 1)
     k_fields_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int nitems, int par) {
   if constexpr (!PERSIST) {
     fields_item<T, SOLID>(doms, __ldg(items + blockIdx.x), par);

@@ -426,6 +426,54 @@ def test_slab_graph_schedule_is_bitwise_equal_to_plain_launches(prec, first):
         assert np.array_equal(out[0][key], out[1][key]), key
 
 
+@pytest.mark.parametrize("sched", [(16, 8), (32, 16), (64, 7), (64, 64), (48, 5)])
+def test_every_schedule_gives_the_same_bits(sched):
+    """The step graphs cut the domain into slabs of `planes` planes with tiles
+    of `tz` planes (cg_set_schedule): 25 steps (chains and single steps of both
+    parities) under each schedule equal the plain launches bit for bit."""
+    from paper_2309_07801_gb300 import cg
+    wl = inputs.translating_droplet(64)
+    fields = inputs.workload_fields(wl, noise=1e-3, seed=6)
+    out = []
+    for mode in ("plain", "sched"):
+        d = cg.Domain(cg.make_params(precision="f32", **wl.params()))
+        d.init(*fields)
+        if mode == "plain":
+            cg.cg_profile_enable(d.h, 25)
+        else:
+            d.set_schedule(*sched)
+        for k in (8, 1, 8, 8):
+            d.step(k)
+        if mode == "sched":
+            assert d.schedule == (sched[0], sched[1], False)
+        out.append(d.macros())
+        d.close()
+    for key in out[0]:
+        assert np.array_equal(out[0][key], out[1][key]), key
+
+
+def test_schedule_tuner_picks_a_candidate_and_keeps_the_bits():
+    """The tuner times the candidate schedules on the first chained steps and
+    keeps one of them; the run equals plain launches bit for bit throughout."""
+    from paper_2309_07801_gb300 import cg
+    wl = inputs.translating_droplet(64)
+    fields = inputs.workload_fields(wl, noise=1e-3, seed=7)
+    d = cg.Domain(cg.make_params(precision="f32", **wl.params()))
+    d.init(*fields)
+    assert d.schedule[2]  # tuning pending
+    n = d.tune()
+    planes, tz, tuning = d.schedule
+    assert not tuning and (planes, tz) in ((16, 8), (32, 16), (64, d.schedule[1]))
+    ref = cg.Domain(cg.make_params(precision="f32", **wl.params()))
+    ref.init(*fields)
+    cg.cg_profile_enable(ref.h, n)
+    ref.step(n)
+    for key, v in ref.macros().items():
+        assert np.array_equal(v, d.macros()[key]), key
+    with pytest.raises(cg.CGError):
+        d.set_schedule(65, 8)  # more planes than the domain has
+
+
 def _readback_runs(make, fields):
     """The same 16 steps with and without host read-backs in between (after
     odd and even step counts); returns the final macroscopic fields of each."""

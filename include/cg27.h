@@ -317,10 +317,10 @@ int cg_destroy(cg_ctx *ctx);
  * other products into FMAs); they never depend on the other members.  The
  * launches are built into CUDA graphs (per step parity; eight steps per graph
  * when enough are requested) in which the groups' passes run concurrently;
- * the z depth of the tiles is tuned online by timing three depths on the
- * first steps after the member set has changed by more than a factor two in
- * cells (those steps are ordinary steps: results do not depend on the
- * depth).
+ * the z depth of the tiles, the grid form and the tile shape (block size)
+ * are tuned online by timing the candidates on the first steps after the
+ * member set has changed by more than a factor two in cells (those steps are
+ * ordinary steps: results do not depend on the schedule).
  *
  * Members must share the batch's precision and kernel variant (walls or none;
  * unit-rate Model D or not), else CG_ERR_UNSUPPORTED.  While a domain is a
@@ -377,6 +377,15 @@ int cg_batch_set_persistent(cg_batch *batch, int32_t mode);
 
 /* The grid form in use (0 or 1). */
 int cg_batch_persistent(cg_batch *batch, int32_t *mode);
+
+/* Tile shape of the z-marching batch passes (the block size and the layout
+ * of their shared-memory rings): 0 = 32 x 8 threads, 1 = 32 x 4 threads, or
+ * -1 to let the online tuner choose (the default; it times every candidate
+ * depth and grid form with both shapes).  Results do not depend on the shape.
+ * CG_ERR_INVALID_ARG for other values.  cg_batch_tile() reports the shape in
+ * use as tile_nx x tile_ny threads. */
+int cg_batch_set_tile(cg_batch *batch, int32_t shape);
+int cg_batch_tile(cg_batch *batch, int32_t *tile_nx, int32_t *tile_ny);
 
 /* Release the batch (waits for its stream; members become free domains). */
 int cg_batch_destroy(cg_batch *batch);

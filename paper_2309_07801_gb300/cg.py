@@ -96,6 +96,8 @@ SIGNATURES = {
     "cg_batch_depth": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "cg_batch_set_persistent": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "cg_batch_persistent": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32)]),
+    "cg_batch_set_tile": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "cg_batch_tile": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "cg_batch_destroy": (ctypes.c_int, [_VP])
 }
 
@@ -429,6 +431,17 @@ def cg_batch_persistent(b) -> int:
     return m.value
 
 
+def cg_batch_set_tile(b, shape: int):
+    _check(lib().cg_batch_set_tile(b, int(shape)))
+
+
+def cg_batch_tile(b):
+    """(threads in x, threads in y) of the tile shape in use."""
+    tx, ty = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(lib().cg_batch_tile(b, ctypes.byref(tx), ctypes.byref(ty)))
+    return tx.value, ty.value
+
+
 def cg_batch_destroy(b):
     _check(lib().cg_batch_destroy(b))
 
@@ -474,6 +487,13 @@ class Batch:
     @property
     def persistent(self) -> int:
         return cg_batch_persistent(self.h)
+
+    def set_tile(self, shape: int):
+        cg_batch_set_tile(self.h, shape)
+
+    @property
+    def tile(self):
+        return cg_batch_tile(self.h)
 
     def __len__(self):
         return cg_batch_size(self.h)

@@ -58,6 +58,17 @@ long long table_items(int max_domains) { return std::max<long long>(1 << 16, 64L
 
 bool has_solid(const cg_ctx* c) { return c->L.solid; }
 
+// tile shapes of the z-marching batch kernels (cg27_step.cuh): 0 = ShapeA
+// (32 x 8 threads), 1 = ShapeB (32 x 4)
+constexpr int NUM_SHAPES = 2;
+int tile_x(int shape) { return shape ? ShapeB::TX : ShapeA::TX; }
+int tile_y(int shape) { return shape ? ShapeB::TY : ShapeA::TY; }
+
+// a schedule of the batch: tile depth, grid form, tile shape
+struct Sched {
+  int tz, persist, shape;
+};
+
 }  // namespace
 
 struct cg_batch {
@@ -80,17 +91,20 @@ struct cg_batch {
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   bool stale[2][2] = {{false, false}, {false, false}};
   bool use_graphs = true;
-  // launch schedule: tile depth and grid form (0: one block per work item,
-  // 1: persistent, a grid of the blocks the GPU holds at once walking the list)
+  // launch schedule: tile depth, grid form (0: one block per work item,
+  // 1: persistent, a grid of the blocks the GPU holds at once walking the
+  // list) and tile shape of the z-marching passes
   int persist = 0;
-  int resident[4] = {0, 0, 0, 0};  // blocks per SM of the four batch kernels
+  int shape = 0;
+  int resident[NUM_SHAPES][4] = {};  // blocks per SM of the four batch kernels, per shape
   int sms = 0;
   // tuning of the schedule
   int fixed_tz = 0;              // > 0: set by the caller, not tuned
   int fixed_persist = -1;        // >= 0: set by the caller, not tuned
+  int fixed_shape = -1;          // >= 0: set by the caller, not tuned
   long long tuned_cells = 0;     // cell count the current choice was tuned for
-  std::vector<std::pair<int, int>> cand;  // (depth, grid form) still to time
-  std::vector<std::pair<double, std::pair<int, int>>> timed;  // (ms per step, candidate)
+  std::vector<Sched> cand;       // schedules still to time
+  std::vector<std::pair<double, Sched>> timed;  // (ms per step, schedule)
   cudaEvent_t ev[2] = {nullptr, nullptr};
   int64_t steps = 0;
 
@@ -127,23 +141,25 @@ int max_nz(const cg_batch* b) {
   return m;
 }
 
-// depth with about eight tiles per SM over the whole batch
+// depth with about eight tiles of the current shape per SM over the whole batch
 int heuristic_tz(const cg_batch* b) {
   int dev = 0, sms = 148;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tx = tile_x(b->shape), ty = tile_y(b->shape);
   long long col_planes = 0;  // sum over members of tiles_xy * nz
   for (const cg_ctx* c : b->members)
-    col_planes += (long long)((c->prm.nx + TX - 1) / TX) * ((c->prm.ny + TY - 1) / TY) * c->prm.nz;
+    col_planes += (long long)((c->prm.nx + tx - 1) / tx) * ((c->prm.ny + ty - 1) / ty) * c->prm.nz;
   const long long want = 8LL * sms;
   return (int)std::max(1LL, std::min<long long>(max_nz(b), (col_planes + want - 1) / want));
 }
 
 // tile items of the members at depth tz (each member's depth capped by its nz)
 long long count_items(const cg_batch* b, int tz) {
+  const int tx = tile_x(b->shape), ty = tile_y(b->shape);
   long long n = 0;
   for (const cg_ctx* c : b->members) {
     const int t = std::min(tz, c->prm.nz);
-    n += (long long)((c->prm.nx + TX - 1) / TX) * ((c->prm.ny + TY - 1) / TY) * ((c->prm.nz + t - 1) / t);
+    n += (long long)((c->prm.nx + tx - 1) / tx) * ((c->prm.ny + ty - 1) / ty) * ((c->prm.nz + t - 1) / t);
   }
   return n;
 }
@@ -170,8 +186,8 @@ int write_table(cg_batch* b) {
     D.P[0] = make_ptrs<T>(c, cur);
     D.P[1] = make_ptrs<T>(c, 1 - cur);
     D.tz = std::min(tz, c->prm.nz);
-    D.tiles_x = (c->prm.nx + TX - 1) / TX;
-    D.tiles_y = (c->prm.ny + TY - 1) / TY;
+    D.tiles_x = (c->prm.nx + tile_x(b->shape) - 1) / tile_x(b->shape);
+    D.tiles_y = (c->prm.ny + tile_y(b->shape) - 1) / tile_y(b->shape);
     D.use_Q = c->prm.use_Q;
     const int chunks = (c->prm.nz + D.tz - 1) / D.tz;
     istart[d] = (int)items.size();
@@ -231,7 +247,8 @@ struct GroupPass {
 unsigned pass_grid(const cg_batch* b, int items, int kernel) {
   if (!b->persist) return (unsigned)items;
   const int ng = (int)b->gdom.size() - 1;
-  const long long share = std::max(1LL, (long long)b->sms * std::max(1, b->resident[kernel]) / std::max(1, ng));
+  const long long share =
+      std::max(1LL, (long long)b->sms * std::max(1, b->resident[b->shape][kernel]) / std::max(1, ng));
   return (unsigned)std::min<long long>(items, share);
 }
 
@@ -251,27 +268,30 @@ GroupPass<T> group_pass(const cg_batch* b, int k) {
   return g;
 }
 
-// the four batch kernels of a variant in one grid form
+// the four batch kernels of a variant in one grid form and tile shape
+template <typename T, typename SF, bool SOLID, bool UNIT, bool PERSIST, class SH>
+void batch_kernels_of(void* fn[4]) {
+  fn[0] = (void*)k_macro_batch<T, SF, SOLID, PERSIST, SH>;
+  fn[1] = (void*)k_fields_batch<T, SOLID, PERSIST, SH>;
+  fn[2] = (void*)k_div_batch<T, PERSIST, SH>;
+  fn[3] = (void*)k_collide_batch<T, SF, SOLID, UNIT, PERSIST>;
+}
 template <typename T, typename SF, bool SOLID, bool UNIT>
-void batch_kernels(bool persist, void* fn[4]) {
+void batch_kernels(bool persist, int shape, void* fn[4]) {
   if (persist) {
-    fn[0] = (void*)k_macro_batch<T, SF, SOLID, true>;
-    fn[1] = (void*)k_fields_batch<T, SOLID, true>;
-    fn[2] = (void*)k_div_batch<T, true>;
-    fn[3] = (void*)k_collide_batch<T, SF, SOLID, UNIT, true>;
+    if (shape) batch_kernels_of<T, SF, SOLID, UNIT, true, ShapeB>(fn);
+    else batch_kernels_of<T, SF, SOLID, UNIT, true, ShapeA>(fn);
   } else {
-    fn[0] = (void*)k_macro_batch<T, SF, SOLID, false>;
-    fn[1] = (void*)k_fields_batch<T, SOLID, false>;
-    fn[2] = (void*)k_div_batch<T, false>;
-    fn[3] = (void*)k_collide_batch<T, SF, SOLID, UNIT, false>;
+    if (shape) batch_kernels_of<T, SF, SOLID, UNIT, false, ShapeB>(fn);
+    else batch_kernels_of<T, SF, SOLID, UNIT, false, ShapeA>(fn);
   }
 }
 
 template <typename T, typename SF, bool SOLID, bool UNIT>
 void launch_step(cg_batch* b, int par) {
-  const dim3 blk(TX, TY, 1), cblk(128, 1, 1);
+  const dim3 blk(tile_x(b->shape), tile_y(b->shape), 1), cblk(128, 1, 1);
   void* fn[4];
-  batch_kernels<T, SF, SOLID, UNIT>(b->persist != 0, fn);
+  batch_kernels<T, SF, SOLID, UNIT>(b->persist != 0, b->shape, fn);
   for (int k = 0; k + 1 < (int)b->gdom.size(); ++k) {
     GroupPass<T> g = group_pass<T>(b, k);
     void* a_tile[] = {(void*)&g.doms, (void*)&g.items, (void*)&g.ntiles, (void*)&par};
@@ -288,11 +308,11 @@ cudaGraph_t build_batch_graph(const cg_batch* b, int par0, int nsteps) {
   cudaGraph_t gph;
   if (cudaGraphCreate(&gph, 0) != cudaSuccess) return nullptr;
   bool ok = true;
-  const dim3 blk(TX, TY, 1), cblk(128, 1, 1);
+  const dim3 blk(tile_x(b->shape), tile_y(b->shape), 1), cblk(128, 1, 1);
   const int ng = (int)b->gdom.size() - 1;
   std::vector<cudaGraphNode_t> last(ng, nullptr);
   void* fn[4];
-  batch_kernels<T, SF, SOLID, UNIT>(b->persist != 0, fn);
+  batch_kernels<T, SF, SOLID, UNIT>(b->persist != 0, b->shape, fn);
   for (int s = 0; s < nsteps && ok; ++s) {
     int par = (par0 + s) & 1;
     for (int k = 0; k < ng && ok; ++k) {
@@ -345,15 +365,16 @@ bool ready_graph(cg_batch* b, int k, int par, int nsteps) {
 
 template <typename T, typename SF, bool SOLID, bool UNIT>
 int run_steps(cg_batch* b, int64_t n) {
-  if (b->resident[0] == 0) {
-    // blocks per SM of the four kernels of this variant (the persistent grids)
+  if (b->resident[b->shape][0] == 0) {
+    // blocks per SM of the four kernels of this variant and shape (the persistent grids)
     int dev = 0;
     CG_CUDA(cudaGetDevice(&dev));
     CG_CUDA(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev));
     void* fn[4];
-    batch_kernels<T, SF, SOLID, UNIT>(true, fn);
+    batch_kernels<T, SF, SOLID, UNIT>(true, b->shape, fn);
+    const int nt = tile_x(b->shape) * tile_y(b->shape);
     for (int p = 0; p < 4; ++p)
-      CG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->resident[p], fn[p], p < 3 ? NT : 128, 0));
+      CG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->resident[b->shape][p], fn[p], p < 3 ? nt : 128, 0));
   }
   for (int64_t s = 0; s < n;) {
     const int par = (int)(b->table_steps & 1);
@@ -401,28 +422,38 @@ int write_table_any(cg_batch* b) {
 }
 
 // Start tuning when the member set has changed by more than a factor two in
-// cells: the candidates are three depths (the heuristic h, h/2, 2h) times the
-// two grid forms, less what the caller has fixed.
+// cells: the candidates are three depths (the heuristic h, h/2, 2h of each
+// tile shape) times the two grid forms times the two tile shapes, less what
+// the caller has fixed.
 void maybe_retune(cg_batch* b) {
   if (b->members.empty()) return;
   const long long n = total_cells(b);
   if (b->tuned_cells > 0 && n <= 2 * b->tuned_cells && 2 * n >= b->tuned_cells) return;
-  std::vector<int> depths, forms;
-  if (b->fixed_tz > 0) {
-    depths.push_back(b->fixed_tz);
-  } else {
-    const int h = heuristic_tz(b), mz = max_nz(b);
-    for (int t : {h, std::max(1, h / 2), std::min(mz, 2 * h)})
-      if (std::find(depths.begin(), depths.end(), t) == depths.end()) depths.push_back(t);
-  }
+  std::vector<int> forms, shapes;
   if (b->fixed_persist >= 0) forms.push_back(b->fixed_persist);
   else forms = {0, 1};
+  if (b->fixed_shape >= 0) shapes.push_back(b->fixed_shape);
+  else shapes = {0, 1};
+  const int keep = b->shape;
   b->cand.clear();
-  for (int t : depths)
-    for (int f : forms) b->cand.push_back({t, f});
+  for (int sh : shapes) {
+    std::vector<int> depths;
+    if (b->fixed_tz > 0) {
+      depths.push_back(b->fixed_tz);
+    } else {
+      b->shape = sh;  // the heuristic counts tiles of this shape
+      const int h = heuristic_tz(b), mz = max_nz(b);
+      for (int t : {h, std::max(1, h / 2), std::min(mz, 2 * h)})
+        if (std::find(depths.begin(), depths.end(), t) == depths.end()) depths.push_back(t);
+    }
+    for (int t : depths)
+      for (int f : forms) b->cand.push_back({t, f, sh});
+  }
+  b->shape = keep;
   if (b->cand.size() == 1) {  // nothing left to choose
-    b->tz = b->cand[0].first;
-    b->persist = b->cand[0].second;
+    b->tz = b->cand[0].tz;
+    b->persist = b->cand[0].persist;
+    b->shape = b->cand[0].shape;
     b->cand.clear();
     b->dirty = true;
   }
@@ -506,7 +537,7 @@ int cg_batch_remove(cg_batch* b, cg_ctx* c) {
   if (b->members.empty()) {
     b->solid = b->unit = -1;
     b->tuned_cells = 0;
-    b->resident[0] = 0;  // the next member may bring another kernel variant
+    for (auto& r : b->resident) r[0] = 0;  // the next member may bring another kernel variant
   } else {
     maybe_retune(b);
   }
@@ -549,6 +580,28 @@ int cg_batch_set_persistent(cg_batch* b, int32_t mode) {
   return CG_OK;
 }
 
+int cg_batch_set_tile(cg_batch* b, int32_t shape) {
+  if (!b) return fail(CG_ERR_INVALID_ARG, "batch is NULL");
+  if (shape < -1 || shape >= NUM_SHAPES) return fail(CG_ERR_INVALID_ARG, "tile must be -1 (tuned), 0 or 1");
+  b->fixed_shape = shape;
+  b->tuned_cells = 0;
+  b->cand.clear();
+  b->timed.clear();
+  if (shape >= 0) {
+    b->shape = shape;
+    b->dirty = true;
+  }
+  maybe_retune(b);
+  return CG_OK;
+}
+
+int cg_batch_tile(cg_batch* b, int32_t* tile_nx, int32_t* tile_ny) {
+  if (!b || !tile_nx || !tile_ny) return fail(CG_ERR_INVALID_ARG, "NULL argument");
+  *tile_nx = tile_x(b->shape);
+  *tile_ny = tile_y(b->shape);
+  return CG_OK;
+}
+
 int cg_batch_persistent(cg_batch* b, int32_t* mode) {
   if (!b || !mode) return fail(CG_ERR_INVALID_ARG, "NULL argument");
   *mode = b->persist;
@@ -575,14 +628,19 @@ int cg_batch_step(cg_batch* b, int64_t nsteps) {
     b->persist = b->fixed_persist;
     b->dirty = true;
   }
+  if (b->fixed_shape >= 0 && b->shape != b->fixed_shape) {
+    b->shape = b->fixed_shape;
+    b->dirty = true;
+  }
   if (b->tz == 0) b->tz = heuristic_tz(b);
   // tuning: time TUNE_STEPS steps per candidate schedule (one untimed step
   // first, for the table write and the graph build)
   while (!b->cand.empty() && nsteps >= TUNE_STEPS + 1) {
-    const std::pair<int, int> t = b->cand.back();
+    const Sched t = b->cand.back();
     b->cand.pop_back();
-    b->tz = t.first;
-    b->persist = t.second;
+    b->tz = t.tz;
+    b->persist = t.persist;
+    b->shape = t.shape;
     if ((rc = write_table_any(b))) return rc;
     if ((rc = run(b, 1))) return rc;
     CG_CUDA(cudaEventRecord(b->ev[0], b->stream));
@@ -594,9 +652,13 @@ int cg_batch_step(cg_batch* b, int64_t nsteps) {
     b->timed.push_back({ms / TUNE_STEPS, t});
     nsteps -= TUNE_STEPS + 1;
     if (b->cand.empty()) {
-      const std::pair<int, int> best = std::min_element(b->timed.begin(), b->timed.end())->second;
-      b->tz = best.first;
-      b->persist = best.second;
+      const Sched best = std::min_element(b->timed.begin(), b->timed.end(),
+                                          [](const std::pair<double, Sched>& x, const std::pair<double, Sched>& y) {
+                                            return x.first < y.first;
+                                          })->second;
+      b->tz = best.tz;
+      b->persist = best.persist;
+      b->shape = best.shape;
       b->dirty = true;
     }
   }

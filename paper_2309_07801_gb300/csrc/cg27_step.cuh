@@ -26,6 +26,17 @@ namespace cg27 {
 
 constexpr int TX = 32, TY = 8, NT = TX * TY;
 
+// Tile shapes of the z-marching passes: TX x TY threads, one per (x, y) column
+// of the tile.  The single-domain kernels use ShapeA; the batch kernels are
+// compiled for both, and the batch tuner chooses (block size 256 or 128, and
+// the shared-memory rings sized for the tile plus its halo).
+template <int X, int Y>
+struct Shape {
+  static constexpr int TX = X, TY = Y, NT = X * Y;
+};
+using ShapeA = Shape<32, 8>;
+using ShapeB = Shape<32, 4>;
+
 __device__ __forceinline__ int wrapi(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
@@ -40,7 +51,9 @@ struct Col {
   int ys[3];   // (y-1, y, y+1) * nx (wrapped)
 };
 
+template <class SH = ShapeA>
 __device__ __forceinline__ Col make_col(const Geom& g, int bx, int by) {
+  constexpr int TX = SH::TX, TY = SH::TY;
   Col c;
   c.tx = threadIdx.x;
   c.ty = threadIdx.y;
@@ -64,8 +77,9 @@ __device__ __forceinline__ int ring3(int z) { return (z + 3) % 3; }
 // Positions of a plane's tile-plus-halo region that this thread loads: at most
 // two per thread for the regions used here; `xy` is the wrapped in-plane cell
 // offset (x + nx y) of each, -1 when unused.  Computed once per block.
-template <int HALO>
+template <int HALO, class SH = ShapeA>
 struct HaloSlots {
+  static constexpr int TX = SH::TX, TY = SH::TY, NT = SH::NT;
   static constexpr int W = TX + 2 * HALO, PL = W * (TY + 2 * HALO);
   static constexpr int K = (PL + NT - 1) / NT;
   int xy[K];
@@ -120,21 +134,26 @@ __device__ __forceinline__ Pr<T> splat(T v) { return pr(v, v); }
 
 // ---- pass 1 -----------------------------------------------------------------------------
 
-template <typename T, typename SF, bool SOLID, int SM = SM_AB>
+template <typename T, typename SF, bool SOLID, int SM = SM_AB, class SH = ShapeA, bool PAIRS = true>
 __device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, const Phys<T>& ph, int z0, int z1,
                                            int bx, int by) {
+  constexpr int NT = SH::NT;
   constexpr int RS = rd_sign<SM>();
-  using HS = HaloSlots<1>;
+  using HS = HaloSlots<1, SH>;
   constexpr int W = HS::W, PL = HS::PL;
   constexpr int NS = 2;  // the colour fractions of the source cells
   constexpr bool SHIFT = Store<SF>::SHIFT;
   using V = Pr<T>;
   // fractions (rho_r/rho, rho_b/rho) of the planes z-1..z+1 plus the one being
-  // loaded, 1-cell halo, as pairs: written by two scalar stores, read by one
-  // 8-byte load
+  // loaded, 1-cell halo.  PAIRS: stored as pairs (two scalar stores, one
+  // 8-byte load per source); else as two arrays (two 4-byte loads), which
+  // needs fewer registers at the load.
   constexpr int RING = 4;
-  __shared__ V sS[RING][PL];
-  const Col c = make_col(g, bx, by);
+  __shared__ __align__(16) T sRaw[RING * NS * PL];
+  auto slot = [&](int r, int f, int i) -> T& {
+    return PAIRS ? sRaw[(r * PL + i) * NS + f] : sRaw[(r * NS + f) * PL + i];
+  };
+  const Col c = make_col<SH>(g, bx, by);
   const long long S = g.stride;
   HS hs;
   hs.init(g, c);
@@ -151,8 +170,8 @@ __device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, cons
 #pragma unroll
     for (int k = 0; k < HS::K; ++k)
       if (hs.xy[k] >= 0) {
-        sS[z & (RING - 1)][c.tid + k * NT].x = pre[k][0];
-        sS[z & (RING - 1)][c.tid + k * NT].y = pre[k][1];
+        slot(z & (RING - 1), 0, c.tid + k * NT) = pre[k][0];
+        slot(z & (RING - 1), 1, c.tid + k * NT) = pre[k][1];
       }
   };
   fetch(z0 - 1);
@@ -181,7 +200,8 @@ __device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, cons
 #pragma unroll
       for (int q = 0; q < 27; ++q) {
         const int src = c.xs[1 - CX(q)] + c.ys[1 - CY(q)] + zo[1 - CZ(q)];
-        const V s = sS[(z - CZ(q) + RING) & (RING - 1)][(c.tx + 1 - CX(q)) + W * (c.ty + 1 - CY(q))];
+        const int rq = (z - CZ(q) + RING) & (RING - 1), iq = (c.tx + 1 - CX(q)) + W * (c.ty + 1 - CY(q));
+        const V s = PAIRS ? reinterpret_cast<const V*>(sRaw)[rq * PL + iq] : pr(slot(rq, 0, iq), slot(rq, 1, iq));
         if (SHIFT) f[q] = pop_decode<true>(q, f[q], s_rest0, ph.rest1);
         T ft = f[q];
         if (SOLID && ((mask >> OPP(q)) & 1u)) {
@@ -214,16 +234,17 @@ __device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, cons
 
 // ---- pass 2 -----------------------------------------------------------------------------
 
-template <typename T, bool SOLID>
+template <typename T, bool SOLID, class SH = ShapeA>
 __device__ __forceinline__ void fields_tile(const Geom& g, const Ptrs<T>& P, const Phys<T>& ph, int z0, int z1,
                                             int bx, int by) {
-  using H2 = HaloSlots<2>;  // phi, 2-cell halo
-  using H1 = HaloSlots<1>;  // n, 1-cell halo
+  constexpr int TX = SH::TX, TY = SH::TY, NT = SH::NT;
+  using H2 = HaloSlots<2, SH>;  // phi, 2-cell halo
+  using H1 = HaloSlots<1, SH>;  // n, 1-cell halo
   constexpr int W2 = H2::W, P2 = H2::PL, W1 = H1::W, P1 = H1::PL;
   __shared__ T sPhi[3][P2];  // phi of three planes (ring3)
   __shared__ T sN[3][3][P1];  // n of three planes (ring3)
   __shared__ T sG[2][3][NT];  // grad phi of the tile cells, planes of parity 0 and 1
-  const Col c = make_col(g, bx, by);
+  const Col c = make_col<SH>(g, bx, by);
   const long long S = g.stride;
   H2 h2;
   h2.init(g, c);
@@ -402,8 +423,9 @@ __device__ __forceinline__ void fields_tile(const Geom& g, const Ptrs<T>& P, con
 // what neighbours read: the pairs (S_z phi, D_z phi) of the plane whose normals
 // come next, and (S_z n_b, D_z n_b) of the output plane, each read as whole
 // 8- or 16-byte records.
-template <int H>
+template <int H, class SH = ShapeA>
 struct RingSlots {
+  static constexpr int TX = SH::TX, TY = SH::TY, NT = SH::NT;
   static constexpr int W = TX + 2 * H, PL = W * (TY + 2 * H), NR = PL - NT;
   static constexpr int K = 1 + (NR + NT - 1) / NT;
   int at[K];   // position in the W-wide plane array, -1 when unused
@@ -444,11 +466,11 @@ __device__ __forceinline__ T fast_rcp(T v) { return T(1) / v; }
 template <>
 __device__ __forceinline__ float fast_rcp<float>(float v) { return __fdividef(1.0f, v); }
 
-template <typename T>
+template <typename T, class SH = ShapeA>
 __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P, const Phys<T>& ph, int z0,
                                                 int z1, int bx, int by) {
-  using R2 = RingSlots<2>;  // phi positions
-  using R1 = RingSlots<1>;  // n positions
+  using R2 = RingSlots<2, SH>;  // phi positions
+  using R1 = RingSlots<1, SH>;  // n positions
   using V = Pr<T>;
   constexpr int W2 = R2::W, P2 = R2::PL, K2 = R2::K, W1 = R1::W, P1 = R1::PL, K1 = R1::K;
   const T S0 = T(2) / T(3), S1 = T(1) / T(6);
@@ -456,7 +478,7 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
   __shared__ float4 sN4[P1];         // (S_z n_0, D_z n_0, S_z n_1, D_z n_1) of the output plane
   __shared__ V sN2[P1];              // (S_z n_2, D_z n_2)
   static_assert(sizeof(T) == 4, "the separable field pass is the FP32 form");
-  const Col c = make_col(g, bx, by);
+  const Col c = make_col<SH>(g, bx, by);
   const long long S = g.stride;
   R2 r2;
   r2.init(g, c);
@@ -656,14 +678,15 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
 // positions in registers and stages only their z parts (S_z for the in-plane
 // components, D_z for the z component) of the output plane in shared memory
 // (two buffers, one barrier per plane).
-template <typename T>
+template <typename T, class SH = ShapeA>
 __device__ __forceinline__ void div_sep_tile(const Geom& g, const Ptrs<T>& P, int z0, int z1, int use_Q, int bx,
                                              int by) {
-  using HS = HaloSlots<1>;
+  constexpr int NT = SH::NT;
+  using HS = HaloSlots<1, SH>;
   constexpr int W = HS::W, PL = HS::PL, K = HS::K;
   constexpr T S0 = T(2) / T(3), S1 = T(1) / T(6);
   __shared__ T sA[2][6][PL];
-  const Col c = make_col(g, bx, by);
+  const Col c = make_col<SH>(g, bx, by);
   const long long S = g.stride;
   HS hs;
   hs.init(g, c);
@@ -931,62 +954,67 @@ __device__ __forceinline__ int find_domain(const int* __restrict__ start, int nd
 // next tile's shared-memory prologue follows the last reads of the previous
 // tile.  (The two forms are separate instantiations: the loop costs the
 // one-item form about 5 % when it is compiled in.)
-template <typename T, typename SF, bool SOLID>
+template <typename T, typename SF, bool SOLID, class SH>
 __device__ __forceinline__ void macro_item(const Dom<T>* __restrict__ doms, int4 t, int par) {
   const Dom<T>& D = doms[t.x];
-  macro_tile<T, SF, SOLID>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
+  macro_tile<T, SF, SOLID, SM_AB, SH, false>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
 }
 
-template <typename T, bool SOLID>
+template <typename T, bool SOLID, class SH>
 __device__ __forceinline__ void fields_item(const Dom<T>* __restrict__ doms, int4 t, int par) {
   const Dom<T>& D = doms[t.x];
   if constexpr (!SOLID && sizeof(T) == 4)
-    fields_sep_tile<T>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
+    fields_sep_tile<T, SH>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
   else
-    fields_tile<T, SOLID>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
+    fields_tile<T, SOLID, SH>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
 }
 
-template <typename T>
+template <typename T, class SH>
 __device__ __forceinline__ void div_item(const Dom<T>* __restrict__ doms, int4 t, int par) {
   const Dom<T>& D = doms[t.x];
-  div_sep_tile<T>(D.g, D.P[par], t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), D.use_Q, t.y, t.z);
+  div_sep_tile<T, SH>(D.g, D.P[par], t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), D.use_Q, t.y, t.z);
 }
 
-template <typename T, typename SF, bool SOLID, bool PERSIST>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !SOLID) ? 4 : 1)
+// blocks per SM that the register caps of the batch kernels aim at: those of
+// the single-domain kernels for 256 threads, twice as many for 128
+template <class SH>
+constexpr int per_sm(int blocks256) { return blocks256 * (256 / SH::NT); }
+
+template <typename T, typename SF, bool SOLID, bool PERSIST, class SH>
+__global__ void __launch_bounds__(SH::NT, per_sm<SH>((sizeof(T) == 4 && !SOLID) ? 4 : 1))
     k_macro_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int nitems, int par) {
   if constexpr (!PERSIST) {
-    macro_item<T, SF, SOLID>(doms, __ldg(items + blockIdx.x), par);
+    macro_item<T, SF, SOLID, SH>(doms, __ldg(items + blockIdx.x), par);
   } else {
     for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
       if (i != (int)blockIdx.x) __syncthreads();
-      macro_item<T, SF, SOLID>(doms, __ldg(items + i), par);
+      macro_item<T, SF, SOLID, SH>(doms, __ldg(items + i), par);
     }
   }
 }
 
-template <typename T, bool SOLID, bool PERSIST>
-__global__ void __launch_bounds__(NT, (!SOLID && sizeof(T) == 4) ? 3 : 1)
+template <typename T, bool SOLID, bool PERSIST, class SH>
+__global__ void __launch_bounds__(SH::NT, per_sm<SH>((!SOLID && sizeof(T) == 4) ? 3 : 1))
     k_fields_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int nitems, int par) {
   if constexpr (!PERSIST) {
-    fields_item<T, SOLID>(doms, __ldg(items + blockIdx.x), par);
+    fields_item<T, SOLID, SH>(doms, __ldg(items + blockIdx.x), par);
   } else {
     for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
       if (i != (int)blockIdx.x) __syncthreads();
-      fields_item<T, SOLID>(doms, __ldg(items + i), par);
+      fields_item<T, SOLID, SH>(doms, __ldg(items + i), par);
     }
   }
 }
 
-template <typename T, bool PERSIST>
-__global__ void __launch_bounds__(NT)
+template <typename T, bool PERSIST, class SH>
+__global__ void __launch_bounds__(SH::NT)
     k_div_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int nitems, int par) {
   if constexpr (!PERSIST) {
-    div_item<T>(doms, __ldg(items + blockIdx.x), par);
+    div_item<T, SH>(doms, __ldg(items + blockIdx.x), par);
   } else {
     for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
       if (i != (int)blockIdx.x) __syncthreads();
-      div_item<T>(doms, __ldg(items + i), par);
+      div_item<T, SH>(doms, __ldg(items + i), par);
     }
   }
 }

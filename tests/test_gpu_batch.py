@@ -144,7 +144,7 @@ def test_batch_depth_does_not_change_results():
         d = cg.Domain(cg.make_params(precision="f32", **params))
         d.init(*fields)
         b.add(d)
-        b.step(10)
+        b.step(20)  # four candidates (grid forms x tile shapes) at the fixed depth, four steps each
         assert b.depth == (tz, False)
         b.remove(d)
         outs.append(d.macros())
@@ -190,6 +190,54 @@ def test_batch_grid_form_does_not_change_results(prec):
     b = cg.Batch(1, prec)
     with pytest.raises(cg.CGError):
         b.set_persistent(2)
+    b.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_batch_tile_shape_does_not_change_results(prec):
+    """The two tile shapes of the z-marching batch passes (32 x 8 and 32 x 4
+    threads: block size and shared-memory rings) give the same bits, in both
+    grid forms, with members of different sizes; the tuner, left alone, picks
+    one of them and reports it."""
+    from paper_2309_07801_gb300 import cg
+    cases = [_case("osc", (48, 40, 24), 4.0, 0.005, 2), _case("static", (33, 30, 35), 2.0, 0.01, 3)]
+    outs = []
+    for shape, mode in ((0, 0), (1, 0), (1, 1)):
+        b = cg.Batch(4, prec)
+        b.set_depth(5)
+        b.set_persistent(mode)
+        b.set_tile(shape)
+        doms = []
+        for params, fields in cases:
+            d = cg.Domain(cg.make_params(precision=prec, **params))
+            d.init(*fields)
+            b.add(d)
+            doms.append(d)
+        b.step(2)
+        b.step(8)
+        assert b.tile == ((32, 8) if shape == 0 else (32, 4))
+        res = []
+        for d in doms:
+            b.remove(d)
+            res.append(d.macros())
+            d.close()
+        b.close()
+        outs.append(res)
+    for other in outs[1:]:
+        for a, c in zip(outs[0], other):
+            for key in a:
+                assert np.array_equal(a[key], c[key]), key
+    b = cg.Batch(2, prec)
+    with pytest.raises(cg.CGError):
+        b.set_tile(2)
+    params, fields = cases[0]
+    d = cg.Domain(cg.make_params(precision=prec, **params))
+    d.init(*fields)
+    b.add(d)
+    b.step(60)  # the tuner times 12 candidate schedules, four steps each
+    assert b.tile in ((32, 8), (32, 4)) and b.depth[1] is False
+    b.remove(d)
+    d.close()
     b.close()
 
 

@@ -378,6 +378,15 @@ int cg_batch_set_persistent(cg_batch *batch, int32_t mode);
 /* The grid form in use (0 or 1). */
 int cg_batch_persistent(cg_batch *batch, int32_t *mode);
 
+/* Step budget of a member: it takes part in the batch's steps until its step
+ * count (cg_steps_taken) reaches total_steps, and sits out the remaining
+ * steps of every later cg_batch_step() call (its work items return at once),
+ * so that members with different step counts share one call and no member
+ * has to stop the others at its own count.  total_steps < 0 removes the
+ * budget (the default, and what joining or leaving a batch sets).  Waits for
+ * the batch's stream.  CG_ERR_INVALID_ARG if the domain is not a member. */
+int cg_batch_set_stop(cg_batch *batch, cg_ctx *ctx, int64_t total_steps);
+
 /* Tile shape of the z-marching batch passes (the block size and the layout
  * of their shared-memory rings): 0 = 32 x 8 threads, 1 = 32 x 4 threads, or
  * -1 to let the online tuner choose (the default; it times every candidate

@@ -97,6 +97,7 @@ SIGNATURES = {
     "cg_batch_set_persistent": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "cg_batch_persistent": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32)]),
     "cg_batch_set_tile": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "cg_batch_set_stop": (ctypes.c_int, [_VP, _VP, ctypes.c_int64]),
     "cg_batch_tile": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "cg_batch_destroy": (ctypes.c_int, [_VP])
 }
@@ -431,6 +432,10 @@ def cg_batch_persistent(b) -> int:
     return m.value
 
 
+def cg_batch_set_stop(b, h, total_steps: int):
+    _check(lib().cg_batch_set_stop(b, h, int(total_steps)))
+
+
 def cg_batch_set_tile(b, shape: int):
     _check(lib().cg_batch_set_tile(b, int(shape)))
 
@@ -487,6 +492,9 @@ class Batch:
     @property
     def persistent(self) -> int:
         return cg_batch_persistent(self.h)
+
+    def set_stop(self, dom: Domain, total_steps: int):
+        cg_batch_set_stop(self.h, dom.h, total_steps)
 
     def set_tile(self, shape: int):
         cg_batch_set_tile(self.h, shape)

@@ -33,7 +33,7 @@ size_t dom_bytes(int precision) {
 }
 
 struct BatchLayout {
-  size_t doms = 0, items = 0, cell_start = 0, total = 0;
+  size_t doms = 0, items = 0, cell_start = 0, tick = 0, total = 0;
   long long max_items = 0;
 };
 
@@ -48,6 +48,8 @@ BatchLayout batch_layout(int max_domains, int precision, long long max_items) {
   L.items = off;
   L.max_items = max_items;
   off = align_up(off + (size_t)max_items * sizeof(int4));
+  L.tick = off;  // step number of the current launch, counted from the table write
+  off = align_up(off + sizeof(int));
   L.total = off;
   return L;
 }
@@ -63,6 +65,9 @@ bool has_solid(const cg_ctx* c) { return c->L.solid; }
 constexpr int NUM_SHAPES = 2;
 int tile_x(int shape) { return shape ? ShapeB::TX : ShapeA::TX; }
 int tile_y(int shape) { return shape ? ShapeB::TY : ShapeA::TY; }
+
+// advances the step number of a batch after a launch of n steps
+__global__ void k_batch_tick(int* tick, int n) { *tick += n; }
 
 // a schedule of the batch: tile depth, grid form, tile shape
 struct Sched {
@@ -116,6 +121,7 @@ struct cg_batch {
       if (e) cudaEventDestroy(e);
     for (cg_ctx* c : members) {
       c->batch = nullptr;
+      c->batch_stop = -1;
       c->batch_stream = nullptr;
     }
   }
@@ -189,6 +195,9 @@ int write_table(cg_batch* b) {
     D.tiles_x = (c->prm.nx + tile_x(b->shape) - 1) / tile_x(b->shape);
     D.tiles_y = (c->prm.ny + tile_y(b->shape) - 1) / tile_y(b->shape);
     D.use_Q = c->prm.use_Q;
+    D.tick = reinterpret_cast<const int*>(b->ws + b->L.tick);
+    const long long left = c->batch_stop < 0 ? (1LL << 30) : std::max<long long>(0, c->batch_stop - c->steps);
+    D.stop = (int)std::min<long long>(left, 1LL << 30);
     const int chunks = (c->prm.nz + D.tz - 1) / D.tz;
     istart[d] = (int)items.size();
     for (int bz = 0; bz < chunks; ++bz)
@@ -222,6 +231,7 @@ int write_table(cg_batch* b) {
                             cudaMemcpyHostToDevice, b->stream));
     CG_CUDA(cudaMemcpyAsync(b->ws + b->L.cell_start, cs.data(), (nd + 1) * sizeof(int),
                             cudaMemcpyHostToDevice, b->stream));
+    CG_CUDA(cudaMemsetAsync(b->ws + b->L.tick, 0, sizeof(int), b->stream));
     CG_CUDA(cudaStreamSynchronize(b->stream));  // the host vectors end here
   }
   b->table_steps = 0;
@@ -300,6 +310,7 @@ void launch_step(cg_batch* b, int par) {
     for (int p = 0; p < 4; ++p)
       cudaLaunchKernel(fn[p], g.grid[p], p < 3 ? blk : cblk, p < 3 ? a_tile : a_coll, 0, b->stream);
   }
+  k_batch_tick<<<1, 1, 0, b->stream>>>(reinterpret_cast<int*>(b->ws + b->L.tick), 1);
 }
 
 // nsteps steps from parity par0: per group a chain of its four passes per step
@@ -314,11 +325,11 @@ cudaGraph_t build_batch_graph(const cg_batch* b, int par0, int nsteps) {
   void* fn[4];
   batch_kernels<T, SF, SOLID, UNIT>(b->persist != 0, b->shape, fn);
   for (int s = 0; s < nsteps && ok; ++s) {
-    int par = (par0 + s) & 1;
+    int sp = (s << 1) | ((par0 + s) & 1);  // step offset within the graph, parity
     for (int k = 0; k < ng && ok; ++k) {
       GroupPass<T> g = group_pass<T>(b, k);
-      void* a_tile[] = {(void*)&g.doms, (void*)&g.items, (void*)&g.ntiles, (void*)&par};
-      void* a_coll[] = {(void*)&g.cdoms, (void*)&g.cs, (void*)&g.ndom, (void*)&par, (void*)&g.block0,
+      void* a_tile[] = {(void*)&g.doms, (void*)&g.items, (void*)&g.ntiles, (void*)&sp};
+      void* a_coll[] = {(void*)&g.cdoms, (void*)&g.cs, (void*)&g.ndom, (void*)&sp, (void*)&g.block0,
                         (void*)&g.nblocks};
       for (int p = 0; p < 4 && ok; ++p) {
         cudaKernelNodeParams kp = {};
@@ -332,6 +343,22 @@ cudaGraph_t build_batch_graph(const cg_batch* b, int par0, int nsteps) {
         last[k] = node;
       }
     }
+  }
+  // the step number advances once every group's last pass is done
+  if (ok) {
+    int* tick = reinterpret_cast<int*>(b->ws + b->L.tick);
+    int n = nsteps;
+    void* a_tick[] = {(void*)&tick, (void*)&n};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void*)k_batch_tick;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.kernelParams = a_tick;
+    std::vector<cudaGraphNode_t> dv;
+    for (cudaGraphNode_t n_ : last)
+      if (n_) dv.push_back(n_);
+    cudaGraphNode_t node = nullptr;
+    if (cudaGraphAddKernelNode(&node, gph, dv.data(), dv.size(), &kp) != cudaSuccess) ok = false;
   }
   if (!ok) {
     cudaGraphDestroy(gph);
@@ -390,7 +417,8 @@ int run_steps(cg_batch* b, int64_t n) {
       for (int i = 0; i < m; ++i) launch_step<T, SF, SOLID, UNIT>(b, (par + i) & 1);
     b->table_steps += m;
     b->steps += m;
-    for (cg_ctx* c : b->members) c->steps += m;
+    for (cg_ctx* c : b->members)
+      c->steps += c->batch_stop < 0 ? m : std::max<int64_t>(0, std::min<int64_t>(m, c->batch_stop - c->steps));
     s += m;
   }
   CG_CUDA(cudaGetLastError());
@@ -519,6 +547,7 @@ int cg_batch_add(cg_batch* b, cg_ctx* c) {
   b->unit = unit;
   b->members.push_back(c);
   c->batch = b;
+  c->batch_stop = -1;
   c->batch_stream = b->stream;
   b->dirty = true;
   maybe_retune(b);
@@ -532,6 +561,7 @@ int cg_batch_remove(cg_batch* b, cg_ctx* c) {
   CG_CUDA(cudaStreamSynchronize(b->stream));  // its last steps are complete
   b->members.erase(it);
   c->batch = nullptr;
+  c->batch_stop = -1;
   c->batch_stream = nullptr;
   b->dirty = true;
   if (b->members.empty()) {
@@ -577,6 +607,16 @@ int cg_batch_set_persistent(cg_batch* b, int32_t mode) {
     b->dirty = true;
   }
   maybe_retune(b);
+  return CG_OK;
+}
+
+int cg_batch_set_stop(cg_batch* b, cg_ctx* c, int64_t total_steps) {
+  if (!b || !c) return fail(CG_ERR_INVALID_ARG, "NULL argument");
+  if (std::find(b->members.begin(), b->members.end(), c) == b->members.end())
+    return fail(CG_ERR_INVALID_ARG, "the domain is not in this batch");
+  CG_CUDA(cudaStreamSynchronize(b->stream));  // the table being replaced may be in use
+  c->batch_stop = total_steps < 0 ? -1 : total_steps;
+  b->dirty = true;
   return CG_OK;
 }
 

@@ -55,6 +55,7 @@ namespace cg27 {
 struct cg_ctx {
   cg_params prm;
   cg_batch* batch = nullptr;  // the batch the domain is a member of, if any
+  int64_t batch_stop = -1;    // step count at which it sits out the batch's steps (-1: none)
   cudaStream_t batch_stream = nullptr;  // and the stream that batch launches on
   cg27::Layout L;
   char* ws = nullptr;

@@ -935,7 +935,18 @@ struct Dom {
   Phys<T> ph;
   Ptrs<T> P[2];  // buffers of the even and odd steps of the batch
   int tz, tiles_x, tiles_y, use_Q;
+  // the member takes part in the batch's steps number < stop, counted from the
+  // table write; *tick is the step number at the start of the current launch
+  const int* tick;
+  int stop;
 };
+
+// `sp` of a batch launch: parity of its buffers in bit 0, its step offset
+// within the launch (graph) above; a member past its stop sits it out
+template <typename T>
+__device__ __forceinline__ bool sits_out(const Dom<T>& D, int sp) {
+  return __ldg(D.tick) + (sp >> 1) >= D.stop;
+}
 
 // largest d with start[d] <= b (start is non-decreasing, start[0] = 0)
 __device__ __forceinline__ int find_domain(const int* __restrict__ start, int ndom, int b) {
@@ -955,14 +966,18 @@ __device__ __forceinline__ int find_domain(const int* __restrict__ start, int nd
 // tile.  (The two forms are separate instantiations: the loop costs the
 // one-item form about 5 % when it is compiled in.)
 template <typename T, typename SF, bool SOLID, class SH>
-__device__ __forceinline__ void macro_item(const Dom<T>* __restrict__ doms, int4 t, int par) {
+__device__ __forceinline__ void macro_item(const Dom<T>* __restrict__ doms, int4 t, int sp) {
   const Dom<T>& D = doms[t.x];
+  if (sits_out(D, sp)) return;
+  const int par = sp & 1;
   macro_tile<T, SF, SOLID, SM_AB, SH, false>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
 }
 
 template <typename T, bool SOLID, class SH>
-__device__ __forceinline__ void fields_item(const Dom<T>* __restrict__ doms, int4 t, int par) {
+__device__ __forceinline__ void fields_item(const Dom<T>* __restrict__ doms, int4 t, int sp) {
   const Dom<T>& D = doms[t.x];
+  if (sits_out(D, sp)) return;
+  const int par = sp & 1;
   if constexpr (!SOLID && sizeof(T) == 4)
     fields_sep_tile<T, SH>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
   else
@@ -970,8 +985,10 @@ __device__ __forceinline__ void fields_item(const Dom<T>* __restrict__ doms, int
 }
 
 template <typename T, class SH>
-__device__ __forceinline__ void div_item(const Dom<T>* __restrict__ doms, int4 t, int par) {
+__device__ __forceinline__ void div_item(const Dom<T>* __restrict__ doms, int4 t, int sp) {
   const Dom<T>& D = doms[t.x];
+  if (sits_out(D, sp)) return;
+  const int par = sp & 1;
   div_sep_tile<T, SH>(D.g, D.P[par], t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), D.use_Q, t.y, t.z);
 }
 
@@ -982,39 +999,39 @@ constexpr int per_sm(int blocks256) { return blocks256 * (256 / SH::NT); }
 
 template <typename T, typename SF, bool SOLID, bool PERSIST, class SH>
 __global__ void __launch_bounds__(SH::NT, per_sm<SH>((sizeof(T) == 4 && !SOLID) ? 4 : 1))
-    k_macro_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int nitems, int par) {
+    k_macro_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int nitems, int sp) {
   if constexpr (!PERSIST) {
-    macro_item<T, SF, SOLID, SH>(doms, __ldg(items + blockIdx.x), par);
+    macro_item<T, SF, SOLID, SH>(doms, __ldg(items + blockIdx.x), sp);
   } else {
     for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
       if (i != (int)blockIdx.x) __syncthreads();
-      macro_item<T, SF, SOLID, SH>(doms, __ldg(items + i), par);
+      macro_item<T, SF, SOLID, SH>(doms, __ldg(items + i), sp);
     }
   }
 }
 
 template <typename T, bool SOLID, bool PERSIST, class SH>
 __global__ void __launch_bounds__(SH::NT, per_sm<SH>((!SOLID && sizeof(T) == 4) ? 3 : 1))
-    k_fields_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int nitems, int par) {
+    k_fields_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int nitems, int sp) {
   if constexpr (!PERSIST) {
-    fields_item<T, SOLID, SH>(doms, __ldg(items + blockIdx.x), par);
+    fields_item<T, SOLID, SH>(doms, __ldg(items + blockIdx.x), sp);
   } else {
     for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
       if (i != (int)blockIdx.x) __syncthreads();
-      fields_item<T, SOLID, SH>(doms, __ldg(items + i), par);
+      fields_item<T, SOLID, SH>(doms, __ldg(items + i), sp);
     }
   }
 }
 
 template <typename T, bool PERSIST, class SH>
 __global__ void __launch_bounds__(SH::NT)
-    k_div_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int nitems, int par) {
+    k_div_batch(const Dom<T>* __restrict__ doms, const int4* __restrict__ items, int nitems, int sp) {
   if constexpr (!PERSIST) {
-    div_item<T, SH>(doms, __ldg(items + blockIdx.x), par);
+    div_item<T, SH>(doms, __ldg(items + blockIdx.x), sp);
   } else {
     for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
       if (i != (int)blockIdx.x) __syncthreads();
-      div_item<T, SH>(doms, __ldg(items + i), par);
+      div_item<T, SH>(doms, __ldg(items + i), sp);
     }
   }
 }
@@ -1022,9 +1039,11 @@ __global__ void __launch_bounds__(SH::NT)
 // collision item blk (batch-wide numbering of start): 128 cells of one domain
 template <typename T, typename SF, bool SOLID, bool UNIT>
 __device__ __forceinline__ void collide_item(const Dom<T>* __restrict__ doms, const int* __restrict__ start,
-                                             int ndom, int par, int blk) {
+                                             int ndom, int sp, int blk) {
   const int d = find_domain(start, ndom, blk);
   const Dom<T>& D = doms[d];
+  if (sits_out(D, sp)) return;
+  const int par = sp & 1;
   // domains hold fewer than 2^31 cells, so 32-bit unsigned index arithmetic is exact
   const unsigned i = (unsigned)(blk - __ldg(start + d)) * 128u + threadIdx.x;
   const unsigned nxy = (unsigned)D.g.nxy, nx = (unsigned)D.g.nx;
@@ -1040,12 +1059,12 @@ __device__ __forceinline__ void collide_item(const Dom<T>* __restrict__ doms, co
 // group has nblocks items
 template <typename T, typename SF, bool SOLID, bool UNIT, bool PERSIST>
 __global__ void __launch_bounds__(128, 6)
-    k_collide_batch(const Dom<T>* __restrict__ doms, const int* __restrict__ start, int ndom, int par,
+    k_collide_batch(const Dom<T>* __restrict__ doms, const int* __restrict__ start, int ndom, int sp,
                     int block0, int nblocks) {
   if constexpr (!PERSIST) {
-    collide_item<T, SF, SOLID, UNIT>(doms, start, ndom, par, (int)blockIdx.x + block0);
+    collide_item<T, SF, SOLID, UNIT>(doms, start, ndom, sp, (int)blockIdx.x + block0);
   } else {
-    for (int b = blockIdx.x; b < nblocks; b += gridDim.x) collide_item<T, SF, SOLID, UNIT>(doms, start, ndom, par, b + block0);
+    for (int b = blockIdx.x; b < nblocks; b += gridDim.x) collide_item<T, SF, SOLID, UNIT>(doms, start, ndom, sp, b + block0);
   }
 }
 

@@ -143,6 +143,7 @@ class Server:
         mass0, _ = dom.mass()
         if self.batch is not None:
             self.batch.add(dom)
+            self.batch.set_stop(dom, req.steps)  # it leaves the shared steps at its own count
         return _Run(req, dom, 0, now, mass0)
 
     def run(self, requests, clock=time.perf_counter) -> dict:
@@ -195,7 +196,11 @@ class Server:
                 if i < len(pending):
                     time.sleep(max(0.0, min(0.05, pending[i].arrival - (clock() - t0))))
                 continue
-            k = min(self.quantum, min(r.req.steps - r.done for r in active))
+            # the quantum ends with the shortest remaining run, rounded up to
+            # whole eight-step chains in the batched mode: a member that
+            # reaches its own count sits out the rest of the quantum
+            shortest = min(r.req.steps - r.done for r in active)
+            k = min(self.quantum, -(-shortest // 8) * 8 if self.batch is not None else shortest)
             if self.batch is not None:
                 self.batch.step(k)
                 # the GPU is busy with the quantum: admit meanwhile
@@ -203,11 +208,12 @@ class Server:
                 self.batch.sync()
             else:
                 for r in active:
-                    r.dom.step(k)
+                    r.dom.step(min(k, r.req.steps - r.done))
                 self.stream.synchronize()
             for r in active:
-                r.done += k
-                cell_updates += k * r.req.cells
+                taken = min(k, r.req.steps - r.done)
+                r.done += taken
+                cell_updates += taken * r.req.cells
             self.log.append((clock() - t0, len(active), k))
             for r in [r for r in active if r.done >= r.req.steps]:
                 if self.batch is not None:

@@ -341,3 +341,47 @@ def test_server_admission_follows_free_device_memory():
     res = srv.run(reqs)
     srv.close()
     assert res["runs"] == len(reqs) and res["max_active"] == 1 and res["nonfinite_runs"] == 0
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_member_step_budget_sits_out_the_rest_of_the_call(prec):
+    """Members with step budgets 5 and 13 and one without share batch steps of
+    3 + 8 + 8 (single steps and chains of both parities): they end at 5, 13 and
+    19 steps, each bit for bit equal to a batch holding it alone for exactly
+    that many steps, and a member that has used its budget is not touched."""
+    from paper_2309_07801_gb300 import cg
+    cases = [_case("osc", (48, 40, 24), 4.0, 0.005, 2), _case("static", (33, 30, 35), 2.0, 0.01, 3),
+             _case("osc", (40, 36, 40), 1.5, 0.008, 4)]
+    budgets = (5, 13, None)
+    b = cg.Batch(4, prec)
+    doms = []
+    for (params, fields), n in zip(cases, budgets):
+        d = cg.Domain(cg.make_params(precision=prec, **params))
+        d.init(*fields)
+        b.add(d)
+        if n is not None:
+            b.set_stop(d, n)
+        doms.append(d)
+    for k in (3, 8, 8):
+        b.step(k)
+    b.sync()
+    got = []
+    for d in doms:
+        got.append((d.steps, d.macros()))
+    for d in doms:
+        b.remove(d)
+        d.close()
+    b.close()
+    assert [g[0] for g in got] == [5, 13, 19]
+    for (params, fields), (n, mac) in zip(cases, got):
+        r = cg.Batch(1, prec)
+        d = cg.Domain(cg.make_params(precision=prec, **params))
+        d.init(*fields)
+        r.add(d)
+        r.step(n)
+        r.remove(d)
+        ref = d.macros()
+        d.close()
+        r.close()
+        for key in ref:
+            assert np.array_equal(ref[key], mac[key]), (n, key)

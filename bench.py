@@ -71,6 +71,8 @@ def parse_args():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other storage modes and in-place streaming")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--schedule", default="",
+                    help="slab,tile planes of the step graphs (default: the library's tuner chooses)")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-rate", type=float, default=3.8,
                     help="Poisson arrivals per second (about 0.8 of the batched capacity)")
@@ -328,6 +330,8 @@ def run_ours(args, dist):
     # the library's schedule tuner times its candidates on the first chained
     # steps; then the chosen schedule's graphs exist (both chain parities) and
     # at least two more chains run before the timed region
+    if args.schedule:
+        d.set_schedule(*map(int, args.schedule.split(",")))
     tune_steps = d.tune()
     schedule = d.schedule[:2]
     d.step(max(W, 2 * GRAPH_STEPS + 1))
@@ -393,7 +397,8 @@ def run_ours(args, dist):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": describe(wl), "cells": N,
                        "schedule": {"slab_planes": schedule[0], "tile_planes": schedule[1],
-                                    "chosen_by": "library tuner, %d warm-up steps" % tune_steps},
+                                    "chosen_by": ("fixed by --schedule" if args.schedule else
+                                                  "library tuner, %d warm-up steps" % tune_steps)},
                        "parallelism": "replicas" if dist.world > 1 else "single",
                        "l2": "inputs larger than L2: populations and recoloring state 2 x %.0f MB" %
                              (N * (27 + 6) * 4 / 1e6)},

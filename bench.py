@@ -93,11 +93,22 @@ def load_peaks():
 
 
 def source_sha():
+    """Hash of the sources k_collide is built from: the device header (moment
+    transforms, collision, addressing) and the collision's part of the step
+    header (collide_cell and the kernel), so that changes to the other passes
+    keep a recorded traffic figure valid."""
     import hashlib
+    csrc = os.path.join(ROOT, "paper_2309_07801_gb300", "csrc")
     h = hashlib.sha256()
-    for name in ("cg27_device.cuh", "cg27_step.cuh", "cg27_host.cuh", "cg27_capi.cu"):
-        with open(os.path.join(ROOT, "paper_2309_07801_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(csrc, "cg27_device.cuh"), "rb") as fh:
+        h.update(fh.read())
+    with open(os.path.join(csrc, "cg27_step.cuh")) as fh:
+        step = fh.read()
+    a = step.index("// ---- pass 4: streaming of the totals and the collision")
+    b = step.index("// ---- kernels of one domain")
+    h.update(step[a:b].encode())
+    k = step.index("k_collide(Geom g, Ptrs<T> P, Phys<T> ph, int zb)")
+    h.update(step[step.rindex("template", 0, k):step.index("\n}\n", k)].encode())
     return h.hexdigest()[:16]
 
 

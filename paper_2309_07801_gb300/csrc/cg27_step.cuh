@@ -517,16 +517,18 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
       if (r1.at[k] < 0) continue;
       const int lx = r1.at[k] % W1, ly = r1.at[k] / W1;
       const int ctr = (lx + 1) + W2 * (ly + 1);
-      V sx[3], dx[3];
+      // rows y-1, y, y+1 in turn: S_y and D_y weights (1/6, 2/3, 1/6) and (-1/2, 0, 1/2)
+      T gx = T(0), gy = T(0), gz = T(0);
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         const V a = sAB[ctr + (r - 1) * W2 - 1], b = sAB[ctr + (r - 1) * W2], d = sAB[ctr + (r - 1) * W2 + 1];
-        sx[r] = fma2(splat(S1), add2(a, d), mul2(splat(S0), b));
-        dx[r] = mul2(splat(T(0.5)), sub2(d, a));
+        const V sx = fma2(splat(S1), add2(a, d), mul2(splat(S0), b));
+        const V dx = mul2(splat(T(0.5)), sub2(d, a));
+        const T ws = r == 1 ? S0 : S1, wd = T(r - 1) * T(0.5);
+        gx += ws * dx.x;
+        if (r != 1) gy += wd * sx.x;
+        gz += ws * sx.y;
       }
-      const T gx = S1 * (dx[0].x + dx[2].x) + S0 * dx[1].x;
-      const T gy = T(0.5) * (sx[2].x - sx[0].x);
-      const T gz = S1 * (sx[0].y + sx[2].y) + S0 * sx[1].y;
       const T g2 = gx * gx + gy * gy + gz * gz;
       const T inv_len = g2 > T(1e-24) ? fast_rsqrt(g2) : T(0);
       n3[R][k][0] = gx * inv_len;
@@ -601,28 +603,28 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
       const int i0 = c.xs[1] + c.ys[1] + z * g.nxy;
       const T nc[3] = {n3[B][0][0], n3[B][0][1], n3[B][0][2]};
       // dn[a][b] = d_a n_b: per row, S_x and D_x of (S_z n_b, D_z n_b)
+      // accumulated row by row, so that only the nine sums stay live
       T dn[3][3];
-      {
-        V sx[3][3], dx[3][3];  // [row][b]
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const int o = cc + (r - 1) * W1;
-          const float4 a4 = sN4[o - 1], b4 = sN4[o], d4 = sN4[o + 1];
-          const V a2 = sN2[o - 1], b2 = sN2[o], d2 = sN2[o + 1];
-          const V av[3] = {pr(a4.x, a4.y), pr(a4.z, a4.w), a2};
-          const V bv[3] = {pr(b4.x, b4.y), pr(b4.z, b4.w), b2};
-          const V dv[3] = {pr(d4.x, d4.y), pr(d4.z, d4.w), d2};
+      for (int a = 0; a < 3; ++a)
 #pragma unroll
-          for (int b = 0; b < 3; ++b) {
-            sx[r][b] = fma2(splat(S1), add2(av[b], dv[b]), mul2(splat(S0), bv[b]));
-            dx[r][b] = mul2(splat(T(0.5)), sub2(dv[b], av[b]));
-          }
-        }
+        for (int b = 0; b < 3; ++b) dn[a][b] = T(0);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const int o = cc + (r - 1) * W1;
+        const float4 a4 = sN4[o - 1], b4 = sN4[o], d4 = sN4[o + 1];
+        const V a2 = sN2[o - 1], b2 = sN2[o], d2 = sN2[o + 1];
+        const V av[3] = {pr(a4.x, a4.y), pr(a4.z, a4.w), a2};
+        const V bv[3] = {pr(b4.x, b4.y), pr(b4.z, b4.w), b2};
+        const V dv[3] = {pr(d4.x, d4.y), pr(d4.z, d4.w), d2};
+        const T ws = r == 1 ? S0 : S1, wd = T(r - 1) * T(0.5);
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-          dn[0][b] = S1 * (dx[0][b].x + dx[2][b].x) + S0 * dx[1][b].x;
-          dn[1][b] = T(0.5) * (sx[2][b].x - sx[0][b].x);
-          dn[2][b] = S1 * (sx[0][b].y + sx[2][b].y) + S0 * sx[1][b].y;
+          const V sx = fma2(splat(S1), add2(av[b], dv[b]), mul2(splat(S0), bv[b]));
+          const V dx = mul2(splat(T(0.5)), sub2(dv[b], av[b]));
+          dn[0][b] += ws * dx.x;
+          if (r != 1) dn[1][b] += wd * sx.x;
+          dn[2][b] += ws * sx.y;
         }
       }
       T div = T(0), nnd = T(0);
@@ -897,13 +899,13 @@ __global__ void __launch_bounds__(NT) k_fields(Geom g, Ptrs<T> P, Phys<T> ph, in
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT, 3) k_fields_sep(Geom g, Ptrs<T> P, Phys<T> ph, int tz, int zb, int ze) {
+__global__ void __launch_bounds__(NT, 4) k_fields_sep(Geom g, Ptrs<T> P, Phys<T> ph, int tz, int zb, int ze) {
   const int z0 = zb + blockIdx.z * tz;
   fields_sep_tile<T>(g, P, ph, z0, min(ze, z0 + tz), blockIdx.x, blockIdx.y);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT) k_div_sep(Geom g, Ptrs<T> P, int tz, int use_Q, int zb, int ze) {
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? 4 : 1) k_div_sep(Geom g, Ptrs<T> P, int tz, int use_Q, int zb, int ze) {
   const int z0 = zb + blockIdx.z * tz;
   div_sep_tile<T>(g, P, z0, min(ze, z0 + tz), use_Q, blockIdx.x, blockIdx.y);
 }

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 using namespace cg27;
@@ -444,6 +445,28 @@ int enqueue_step_any(cg_ctx* c, int64_t remaining) {
   }
 }
 
+// The first cell whose densities are not finite and >= 0, or -1: the host
+// arrays are scanned in parallel slices (one per hardware thread, at most 32),
+// so that a 512^3 upload does not wait for one core to read 2 GB.
+long long first_invalid_density(const double* rr, const double* rb, long long n) {
+  auto scan = [rr, rb](long long lo, long long hi) -> long long {
+    for (long long i = lo; i < hi; ++i)
+      if (!(std::isfinite(rr[i]) && std::isfinite(rb[i]) && rr[i] >= 0 && rb[i] >= 0)) return i;
+    return -1;
+  };
+  const int nt = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  if (n < (1LL << 20) || nt == 1) return scan(0, n);
+  std::vector<long long> found(nt, -1);
+  std::vector<std::thread> pool;
+  const long long per = (n + nt - 1) / nt;
+  for (int t = 0; t < nt; ++t)
+    pool.emplace_back([&, t] { found[t] = scan(std::min(n, t * per), std::min(n, (t + 1) * per)); });
+  for (std::thread& th : pool) th.join();
+  for (long long f : found)
+    if (f >= 0) return f;  // slices are in cell order: the first hit is the first invalid cell
+  return -1;
+}
+
 // Device memory free between steps, for staging host transfers: the
 // population buffer the next step writes, or with in-place streaming the
 // recoloring-state buffer the next step writes.  Transfers go through it in
@@ -648,10 +671,9 @@ int cg_init_fields(cg_ctx* c, const double* rho_r, const double* rho_b, const do
   if (solid && !c->L.solid)
     return fail(CG_ERR_INVALID_ARG, "a solid mask needs params.solid_mask = 1 or a bounce-back axis");
   const long long n = c->L.n;
-  for (long long i = 0; i < n; ++i) {
-    if (!(std::isfinite(rho_r[i]) && std::isfinite(rho_b[i]) && rho_r[i] >= 0 && rho_b[i] >= 0))
-      return fail(CG_ERR_INVALID_ARG, "densities must be finite and >= 0 (cell " + std::to_string(i) + ")");
-  }
+  const long long bad = first_invalid_density(rho_r, rho_b, n);
+  if (bad >= 0)
+    return fail(CG_ERR_INVALID_ARG, "densities must be finite and >= 0 (cell " + std::to_string(bad) + ")");
   c->steps = 0;  // the state goes to buffer 0, the staging to buffer 1
   const Stage st = stage_of(c);
   double* d_in = reinterpret_cast<double*>(st.p);

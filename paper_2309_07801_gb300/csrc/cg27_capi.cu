@@ -204,11 +204,15 @@ void start_tuning(cg_ctx* c) {
 }
 
 // the macroscopic pass and the collision of a step of stream mode sm
+// (with two buffers and 8 stride + nx ny < 2^31, the form with 32-bit column
+// offsets: 512^3 fits)
 template <typename T, typename SF, bool SOLID>
-void* macro_kernel(int sm) {
+void* macro_kernel(const cg_ctx* c, int sm) {
   if (sm == SM_EVEN) return (void*)k_macro<T, SF, SOLID, SM_EVEN>;
   if (sm == SM_ODD) return (void*)k_macro<T, SF, SOLID, SM_ODD>;
-  return (void*)k_macro<T, SF, SOLID, SM_AB>;
+  if (8LL * c->L.stride + (long long)c->prm.nx * c->prm.ny < (1LL << 31))
+    return (void*)k_macro<T, SF, SOLID, SM_AB, true>;
+  return (void*)k_macro<T, SF, SOLID, SM_AB, false>;
 }
 template <typename T, typename SF, bool SOLID>
 void* collide_kernel(int sm, bool unit) {
@@ -234,7 +238,7 @@ void launch_passes(cg_ctx* c, int cur, cudaEvent_t* ev, int zb, int ze) {
   {
     int tz_ = tz;
     void* args[] = {(void*)&g, (void*)&P, (void*)&ph, (void*)&tz_, (void*)&zb, (void*)&ze};
-    cudaLaunchKernel(macro_kernel<T, SF, SOLID>(sm), gr, b, args, 0, c->stream);
+    cudaLaunchKernel(macro_kernel<T, SF, SOLID>(c, sm), gr, b, args, 0, c->stream);
   }
   if (ev) cudaEventRecord(ev[1], c->stream);
   if constexpr (!SOLID && sizeof(T) == 4)
@@ -307,7 +311,7 @@ cudaGraphExec_t build_slab_graph(cg_ctx* c, int cur0, int nsteps) {
       const dim3 gr((c->prm.nx + TX - 1) / TX, (c->prm.ny + TY - 1) / TY, (ze[i] - zb[i] + tzs[i] - 1) / tzs[i]);
       void* args[] = {(void*)&g, (void*)&Pc, (void*)&ph, (void*)&tzs[i], (void*)&zb[i], (void*)&ze[i]};
       if (s > 0) deps3(Cprev, i, dv); else dv.clear();
-      add(&M[i], macro_kernel<T, SF, SOLID>(sm), gr, b, args, dv);
+      add(&M[i], macro_kernel<T, SF, SOLID>(c, sm), gr, b, args, dv);
     }
     for (int i = 0; i < ns; ++i) {
       const dim3 gr((c->prm.nx + TX - 1) / TX, (c->prm.ny + TY - 1) / TY, (ze[i] - zb[i] + tzs[i] - 1) / tzs[i]);

@@ -134,9 +134,15 @@ __device__ __forceinline__ Pr<T> splat(T v) { return pr(v, v); }
 
 // ---- pass 1 -----------------------------------------------------------------------------
 
-template <typename T, typename SF, bool SOLID, int SM = SM_AB, class SH = ShapeA, bool PAIRS = true>
+// OFF32 (two buffers only, and 8 stride + nx ny < 2^31): each pulled load is
+// one row base pointer per z offset (three per plane) plus a 32-bit offset per
+// (c_x, c_y) column computed once per thread, instead of a 64-bit address
+// formed per direction.
+template <typename T, typename SF, bool SOLID, int SM = SM_AB, class SH = ShapeA, bool PAIRS = true,
+          bool OFF32 = false>
 __device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, const Phys<T>& ph, int z0, int z1,
                                            int bx, int by) {
+  static_assert(!OFF32 || SM == SM_AB, "32-bit column offsets are for two population buffers");
   constexpr int NT = SH::NT;
   constexpr int RS = rd_sign<SM>();
   using HS = HaloSlots<1, SH>;
@@ -174,6 +180,12 @@ __device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, cons
         slot(z & (RING - 1), 1, c.tid + k * NT) = pre[k][1];
       }
   };
+  // OFF32: element offset of direction j = (c_x + 1) + 3 (c_y + 1) of each z
+  // group from the group's row base, the source column x - c_q included
+  int off[9];
+  if constexpr (OFF32)
+#pragma unroll
+    for (int j = 0; j < 9; ++j) off[j] = j * (int)S + c.xs[1 - (j % 3 - 1)] + c.ys[1 - (j / 3 - 1)];
   fetch(z0 - 1);
   store(z0 - 1 + RING);
   fetch(z0);
@@ -188,10 +200,19 @@ __device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, cons
                          (z == g.nz - 1 ? 0 : z + 1) * g.nxy};
       const int i0 = c.xs[1] + c.ys[1] + zo[1];
       T f[27];
+      if constexpr (OFF32) {
+        // z group k = c_z + 1 pulls from plane z - c_z
+        const SF* base[3];
 #pragma unroll
-      for (int q = 0; q < 27; ++q)
-        f[q] = Store<SF>::template get<T>(fin<SF>(P.f_in) + rd_dir<SM>(q) * S +
-                                          (c.xs[1 + RS * CX(q)] + c.ys[1 + RS * CY(q)] + zo[1 + RS * CZ(q)]));
+        for (int k = 0; k < 3; ++k) base[k] = fin<SF>(P.f_in) + 9LL * k * S + zo[2 - k];
+#pragma unroll
+        for (int q = 0; q < 27; ++q) f[q] = Store<SF>::template get<T>(base[q / 9] + off[q % 9]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 27; ++q)
+          f[q] = Store<SF>::template get<T>(fin<SF>(P.f_in) + rd_dir<SM>(q) * S +
+                                            (c.xs[1 + RS * CX(q)] + c.ys[1 + RS * CY(q)] + zo[1 + RS * CZ(q)]));
+      }
       const uint32_t mask = SOLID ? ld(P.mask + i0) : 0u;
       const T s_rest0 = SHIFT ? ld(P.s_in + S_REST * S + i0) : T(0);
       // sum over q of (w_q / c_s^2) c_q . R(x - c_q), from the divergence pass
@@ -217,11 +238,12 @@ __device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, cons
         if (CY(q) != 0) jy += T(CY(q)) * ft;
         if (CZ(q) != 0) jz += T(CZ(q)) * ft;
       }
-      P.mac[i0] = rr;
-      P.mac[S + i0] = rb;
-      P.mac[2 * S + i0] = jx;
-      P.mac[3 * S + i0] = jy;
-      P.mac[4 * S + i0] = jz;
+      T* const mac = P.mac + i0;  // fields S apart
+      mac[0] = rr;
+      mac[S] = rb;
+      mac[2 * S] = jx;
+      mac[3 * S] = jy;
+      mac[4 * S] = jz;
       const bool self_solid = SOLID && ((mask >> SELF_SOLID_BIT) & 1u);
       P.phi[i0] = self_solid ? T(0) : order_parameter(rr, rb, ph);
       if (!isfinite(rr + rb)) atomicOr(P.flag, 1u);
@@ -580,9 +602,9 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
   T mac[5];
   auto fetch_mac = [&](int z) {
     if (!c.active) return;
-    const int i0 = c.xs[1] + c.ys[1] + zoff(g, z);
+    const T* m = P.mac + (c.xs[1] + c.ys[1] + zoff(g, z));
 #pragma unroll
-    for (int f = 0; f < 5; ++f) mac[f] = ld(P.mac + f * S + i0);
+    for (int f = 0; f < 5; ++f) mac[f] = ld(m + f * S);
   };
   fetch_mac(z0);
   const int cc = (c.tx + 1) + W1 * (c.ty + 1);  // this thread's tile cell among the n positions
@@ -692,19 +714,24 @@ __device__ __forceinline__ void div_sep_tile(const Geom& g, const Ptrs<T>& P, in
   const long long S = g.stride;
   HS hs;
   hs.init(g, c);
-  // components 0-2: (p - rho c_s^2) u, 3-5: R
+  // components 0-2: (p - rho c_s^2) u, 3-5: R; base pointers of the six
+  // fields, so that each load adds one 32-bit cell index
+  const T* src[6] = {P.wv, P.wv + S, P.wv + 2 * S, P.s_out + 2 * S, P.s_out + 3 * S, P.s_out + 4 * S};
   T lo[K][6], mid[K][6], hi[K][6], nx[K][6];
   auto fetch = [&](int z, T (&dst)[K][6]) {
     const int zo = zoff(g, z);
 #pragma unroll
     for (int k = 0; k < K; ++k)
       if (hs.xy[k] >= 0) {
+        const int i = hs.xy[k] + zo;
 #pragma unroll
-        for (int f = 0; f < 3; ++f) dst[k][f] = use_Q ? ld(P.wv + f * S + hs.xy[k] + zo) : T(0);
+        for (int f = 0; f < 3; ++f) dst[k][f] = use_Q ? ld(src[f] + i) : T(0);
 #pragma unroll
-        for (int f = 0; f < 3; ++f) dst[k][3 + f] = P.s_out[(2 + f) * S + hs.xy[k] + zo];
+        for (int f = 3; f < 6; ++f) dst[k][f] = src[f][i];
       }
   };
+  T* const qc[3] = {P.qc, P.qc + S, P.qc + 2 * S};
+  T* const divr = P.s_out + S_DIVR * S;
   fetch(z0 - 1, lo);
   fetch(z0, mid);
   fetch(z0 + 1, hi);
@@ -741,11 +768,11 @@ __device__ __forceinline__ void div_sep_tile(const Geom& g, const Ptrs<T>& P, in
       }
       const int i0 = c.xs[1] + c.ys[1] + z * g.nxy;
       if (use_Q) {
-        P.qc[i0] = T(-3) * d[0][0];
-        P.qc[S + i0] = T(-3) * d[0][1];
-        P.qc[2 * S + i0] = T(-3) * d[0][2];
+        qc[0][i0] = T(-3) * d[0][0];
+        qc[1][i0] = T(-3) * d[0][1];
+        qc[2][i0] = T(-3) * d[0][2];
       }
-      P.s_out[S_DIVR * S + i0] = -(d[1][0] + d[1][1] + d[1][2]);
+      divr[i0] = -(d[1][0] + d[1][1] + d[1][2]);
     }
 #pragma unroll
     for (int k = 0; k < K; ++k)
@@ -885,11 +912,11 @@ __device__ __forceinline__ void collide_cell(const Geom& g, const Ptrs<T>& P, co
 // in x, tiles in y, chunks of tz planes) of TX x TY blocks for the z-marching
 // passes; one thread per cell, one z plane per blockIdx.z, for the collision.
 
-template <typename T, typename SF, bool SOLID, int SM = SM_AB>
+template <typename T, typename SF, bool SOLID, int SM = SM_AB, bool OFF32 = false>
 __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !SOLID) ? 4 : 1)
     k_macro(Geom g, Ptrs<T> P, Phys<T> ph, int tz, int zb, int ze) {
   const int z0 = zb + blockIdx.z * tz;
-  macro_tile<T, SF, SOLID, SM>(g, P, ph, z0, min(ze, z0 + tz), blockIdx.x, blockIdx.y);
+  macro_tile<T, SF, SOLID, SM, ShapeA, true, OFF32>(g, P, ph, z0, min(ze, z0 + tz), blockIdx.x, blockIdx.y);
 }
 
 template <typename T, bool SOLID>

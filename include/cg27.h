@@ -323,7 +323,8 @@ int cg_destroy(cg_ctx *ctx);
  * ordinary steps: results do not depend on the schedule).
  *
  * Members must share the batch's precision and kernel variant (walls or none;
- * unit-rate Model D or not), else CG_ERR_UNSUPPORTED.  While a domain is a
+ * unit-rate Model D or not) and hold at most about 238 million cells (the
+ * batch kernels use 32-bit population offsets), else CG_ERR_UNSUPPORTED.  While a domain is a
  * member, cg_step(), cg_init_fields(), cg_load_state() and cg_destroy() on it
  * fail with CG_ERR_INVALID_ARG; the read calls (cg_read_macros,
  * cg_read_populations, cg_reduce, cg_save_state) first wait for the batch's

@@ -537,6 +537,9 @@ int cg_batch_add(cg_batch* b, cg_ctx* c) {
   if (c->prm.streaming != CG_STREAM_TWO_BUFFERS)
     return fail(CG_ERR_UNSUPPORTED, "batches hold domains with two population buffers");
   if ((int)b->members.size() >= b->max_domains) return fail(CG_ERR_INVALID_ARG, "the batch is full");
+  // the batch kernels address populations with 32-bit column offsets
+  if (8LL * c->L.stride + (long long)c->prm.nx * c->prm.ny >= (1LL << 31))
+    return fail(CG_ERR_UNSUPPORTED, "batch members hold at most about 238 million cells");
   const int solid = has_solid(c) ? 1 : 0, unit = c->unit ? 1 : 0;
   if (!b->members.empty() && (solid != b->solid || unit != b->unit))
     return fail(CG_ERR_UNSUPPORTED,

@@ -999,7 +999,7 @@ __device__ __forceinline__ void macro_item(const Dom<T>* __restrict__ doms, int4
   const Dom<T>& D = doms[t.x];
   if (sits_out(D, sp)) return;
   const int par = sp & 1;
-  macro_tile<T, SF, SOLID, SM_AB, SH, false>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
+  macro_tile<T, SF, SOLID, SM_AB, SH, true, true>(D.g, D.P[par], D.ph, t.w * D.tz, min(D.g.nz, (t.w + 1) * D.tz), t.y, t.z);
 }
 
 template <typename T, bool SOLID, class SH>

@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define CG27_ABI_VERSION 4
+#define CG27_ABI_VERSION 5
 
 /* return codes */
 #define CG_OK 0
@@ -192,9 +192,30 @@ int cg_step(cg_ctx *ctx, int64_t nsteps);
  * cg_set_schedule(ctx, planes, tz) fixes it (1 <= planes <= nz,
  * 1 <= tz <= planes), cg_set_schedule(ctx, 0, 0) starts tuning again; both
  * wait for the domain's stream.  cg_schedule() reports the schedule in use
- * (0, 0 before the first graph step) and whether tuning is under way. */
+ * (0, 0 before the first graph step) and whether tuning is under way.
+ *
+ * Step form.  FP32 domains with two population buffers and no walls (and
+ * 8 * stride + nx * ny < 2^31, stride = N rounded up to 64) can also run the
+ * step as three passes: the collision of step t forms, in the same kernel,
+ * the pulled colour and momentum sums of step t+1 (Sec. II.A streaming and
+ * Eq. (recoloring) applied to the post-collision populations), so the
+ * macroscopic pass and its second read of the populations leave the step.
+ * Its tiles recompute a one-cell ring and one plane above and below (tiles of
+ * fused_tz planes); the sums are added in the order of the macroscopic pass,
+ * and the results are the same as with the four passes, bit for bit.  The
+ * tuner times each candidate above in both forms where the domain can take
+ * the fused one.  cg_set_schedule_form(ctx, planes, tz, fused_tz) fixes the
+ * schedule and the form (fused_tz = 0: four passes; 1 <= fused_tz <= planes:
+ * the fused pass; it also applies to the plain launches of domains below 32
+ * planes or under per-pass timing), all 0 starts tuning again;
+ * CG_ERR_UNSUPPORTED for fused_tz > 0 on a domain that cannot take it.
+ * cg_set_schedule(ctx, p, tz) is cg_set_schedule_form(ctx, p, tz, 0).
+ * cg_schedule_form() reports the form too.  Such a domain holds a second copy
+ * of rho_r, rho_b, j (20 more bytes per cell). */
 int cg_set_schedule(cg_ctx *ctx, int32_t planes, int32_t tz);
 int cg_schedule(cg_ctx *ctx, int32_t *planes, int32_t *tz, int32_t *tuning);
+int cg_set_schedule_form(cg_ctx *ctx, int32_t planes, int32_t tz, int32_t fused_tz);
+int cg_schedule_form(cg_ctx *ctx, int32_t *planes, int32_t *tz, int32_t *fused_tz, int32_t *tuning);
 
 /* Copy the fields of the latest post-streaming state to host arrays (each may
  * be NULL): rho_r[N], rho_b[N], u[3N] (Eq. for rho u, including F/2), p[N]

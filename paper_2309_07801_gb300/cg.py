@@ -78,6 +78,9 @@ SIGNATURES = {
     "cg_set_schedule": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
     "cg_schedule": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                    ctypes.POINTER(ctypes.c_int32)]),
+    "cg_set_schedule_form": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "cg_schedule_form": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "cg_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "cg_profile_read": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_int64)]),
     "cg_mass_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_int32, _VP, _VP]),
@@ -225,6 +228,18 @@ def cg_schedule(h):
     return a.value, b.value, bool(t.value)
 
 
+def cg_set_schedule_form(h, planes: int, tz: int, fused_tz: int):
+    _check(lib().cg_set_schedule_form(h, int(planes), int(tz), int(fused_tz)))
+
+
+def cg_schedule_form(h):
+    """(planes, tz, fused_tz, tuning): the schedule and the step form
+    (fused_tz = 0: four passes, else the fused collision pass)."""
+    a, b, f, t = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(lib().cg_schedule_form(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(f), ctypes.byref(t)))
+    return a.value, b.value, f.value, bool(t.value)
+
+
 def cg_profile_enable(h, max_steps: int):
     _check(lib().cg_profile_enable(h, int(max_steps)))
 
@@ -358,8 +373,14 @@ class Domain:
     def schedule(self):
         return cg_schedule(self.h)
 
-    def set_schedule(self, planes: int, tz: int):
-        cg_set_schedule(self.h, planes, tz)
+    def set_schedule(self, planes: int, tz: int, fused_tz: int = 0):
+        """Fix the schedule (and the step form: fused_tz > 0 takes the fused
+        collision pass with tiles of fused_tz planes); all 0: tune again."""
+        cg_set_schedule_form(self.h, planes, tz, fused_tz)
+
+    @property
+    def schedule_form(self):
+        return cg_schedule_form(self.h)
 
     def tune(self, max_steps: int = 400) -> int:
         """Step until the schedule tuner has chosen (at most max_steps steps);

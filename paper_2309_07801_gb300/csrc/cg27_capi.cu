@@ -127,7 +127,12 @@ Layout make_layout(const cg_params& p) {
     for (int b = 0; b < 2; ++b) L.aux[b] = (b && L.inplace) ? L.aux[0] : take(L.nq * field);
     L.mask = take((size_t)L.stride * 4);
   }
-  L.mac = take(5 * field);
+  // the fused collision pass (FP32, periodic, two buffers, 32-bit pulled
+  // offsets) writes the next step's sums while the current ones are read
+  L.fusable = p.lattice == CG_D3Q27 && p.precision == CG_F32 && !L.solid && !L.inplace &&
+              8LL * L.stride + (long long)p.nx * p.ny < (1LL << 31);
+  L.mac[0] = take(5 * field);
+  L.mac[1] = L.fusable ? take(5 * field) : L.mac[0];
   L.phi = take(field);
   L.qc = take(3 * field);
   L.force = take(3 * field);
@@ -166,15 +171,33 @@ constexpr int GRAPH_STEPS = 8;
 // chains of each candidate: one untimed, then TUNE_CHAINS timed
 constexpr int TUNE_CHAINS = 2;
 
-// candidate schedules (planes, tz) of a domain with nz >= SLAB_MIN_NZ: thin
-// slabs where the domain holds at least two, and whole-domain kernels with the
-// domain's default depth
-std::vector<std::pair<int, int>> schedule_candidates(const cg_ctx* c) {
-  std::vector<std::pair<int, int>> v;
+// planes per tile of the fused collision pass over a whole domain: the
+// deepest of 64, 32, 16 that still gives four blocks per SM (two resident,
+// two waves), else 8 -- the pass recomputes two planes per tile
+int fused_depth(const cg_ctx* c, int planes) {
+  const long long tiles = (long long)((c->prm.nx + FX - 1) / FX) * ((c->prm.ny + FY - 1) / FY);
+  int sms = 148;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  for (int d : {64, 32, 16})
+    if (d <= planes && tiles * ((planes + d - 1) / d) >= 4LL * sms) return d;
+  return std::min(8, planes);
+}
+
+// candidate schedules of a domain with nz >= SLAB_MIN_NZ: thin slabs where the
+// domain holds at least two, and whole-domain kernels with the domain's
+// default depth; each with the four passes and, where the domain can take
+// it, with the fused collision pass (one tile per slab for slabs)
+std::vector<StepSched> schedule_candidates(const cg_ctx* c) {
+  std::vector<StepSched> v;
   const int nz = c->prm.nz;
   for (auto pt : {std::make_pair(16, 8), std::make_pair(32, 16), std::make_pair(64, 32)})
-    if (nz >= 2 * pt.first) v.push_back(pt);
-  v.push_back({nz, std::min(c->tz, nz)});
+    if (nz >= 2 * pt.first) {
+      v.push_back({pt.first, pt.second, 0});
+      if (c->L.fusable) v.push_back({pt.first, pt.second, pt.first});
+    }
+  v.push_back({nz, std::min(c->tz, nz), 0});
+  if (c->L.fusable) v.push_back({nz, std::min(c->tz, nz), fused_depth(c, nz)});
   return v;
 }
 
@@ -187,11 +210,12 @@ void drop_graphs(cg_ctx* c) {
       }
 }
 
-// switch the graph path to schedule (planes, tz); its graphs are built at the next step
-void set_schedule(cg_ctx* c, int planes, int tz) {
-  if (c->sched_planes != planes || c->sched_tz != tz) drop_graphs(c);
-  c->sched_planes = planes;
-  c->sched_tz = tz;
+// switch the graph path to schedule sc; its graphs are built at the next step
+void set_schedule(cg_ctx* c, const StepSched& sc) {
+  if (c->sched_planes != sc.planes || c->sched_tz != sc.tz || c->sched_ftz != sc.ftz) drop_graphs(c);
+  c->sched_planes = sc.planes;
+  c->sched_tz = sc.tz;
+  c->sched_ftz = sc.ftz;
 }
 
 // (re)start tuning: the candidates are timed by the next chained steps
@@ -199,7 +223,7 @@ void start_tuning(cg_ctx* c) {
   c->sched_cand = schedule_candidates(c);
   c->sched_timed.clear();
   c->tune_phase = 0;
-  set_schedule(c, c->sched_cand.front().first, c->sched_cand.front().second);
+  set_schedule(c, c->sched_cand.front());
   if (c->sched_cand.size() == 1) c->sched_cand.clear();  // nothing to choose
 }
 
@@ -223,10 +247,44 @@ void* collide_kernel(int sm, bool unit) {
   return unit ? (void*)k_collide<T, SF, SOLID, true, SM_AB> : (void*)k_collide<T, SF, SOLID, false, SM_AB>;
 }
 
+// whether the steps of the domain take the fused collision pass now
+template <typename T, typename SF, bool SOLID>
+bool fused_now(const cg_ctx* c) {
+  if constexpr (std::is_same<T, float>::value && std::is_same<SF, float>::value && !SOLID)
+    return c->L.fusable && c->sched_ftz > 0;
+  return false;
+}
+
+// the fused collision pass over planes zb <= z < ze in tiles of ftz planes
+void* fused_kernel(const cg_ctx* c) {
+  return c->unit ? (void*)k_collide_macro<true> : (void*)k_collide_macro<false>;
+}
+dim3 fused_grid(const cg_ctx* c, int planes, int ftz) {
+  return dim3((c->prm.nx + FX - 1) / FX, (c->prm.ny + FY - 1) / FY, (planes + ftz - 1) / ftz);
+}
+
+// the macroscopic pass of the whole domain for the step that reads buffer
+// `cur` (the first step of the fused form after anything else)
+template <typename T, typename SF, bool SOLID>
+void launch_macro(cg_ctx* c, int cur) {
+  const Geom g = make_geom(c);
+  const dim3 b(TX, TY, 1);
+  int zb = 0, ze = c->prm.nz, tz = std::min(c->tz, ze);
+  const dim3 gr((c->prm.nx + TX - 1) / TX, (c->prm.ny + TY - 1) / TY, (ze + tz - 1) / tz);
+  const Ptrs<T> P = make_ptrs<T>(c, cur);
+  const Phys<T> ph = make_phys<T>(c->prm);
+  void* args[] = {(void*)&g, (void*)&P, (void*)&ph, (void*)&tz, (void*)&zb, (void*)&ze};
+  cudaLaunchKernel(macro_kernel<T, SF, SOLID>(c, next_mode(c->L.inplace, cur)), gr, b, args, 0, c->stream);
+}
+
+// One step of the whole domain as plain launches: the four passes, or with
+// the fused form fields, div and the fused collision pass (preceded by the
+// macroscopic pass when no fused step left this step's sums).
 template <typename T, typename SF, bool SOLID>
 void launch_passes(cg_ctx* c, int cur, cudaEvent_t* ev, int zb, int ze) {
   const Geom g = make_geom(c);
   const dim3 b(TX, TY, 1);
+  const bool fused = fused_now<T, SF, SOLID>(c);
   const int tz = std::min(c->tz, ze - zb);
   const dim3 gr((c->prm.nx + TX - 1) / TX, (c->prm.ny + TY - 1) / TY, (ze - zb + tz - 1) / tz);
   const dim3 bc = block_of(c->prm);
@@ -235,7 +293,7 @@ void launch_passes(cg_ctx* c, int cur, cudaEvent_t* ev, int zb, int ze) {
   const Phys<T> ph = make_phys<T>(c->prm);
   const int sm = next_mode(c->L.inplace, cur);
   if (ev) cudaEventRecord(ev[0], c->stream);
-  {
+  if (!fused || c->mac_ready != c->steps) {
     int tz_ = tz;
     void* args[] = {(void*)&g, (void*)&P, (void*)&ph, (void*)&tz_, (void*)&zb, (void*)&ze};
     cudaLaunchKernel(macro_kernel<T, SF, SOLID>(c, sm), gr, b, args, 0, c->stream);
@@ -248,9 +306,15 @@ void launch_passes(cg_ctx* c, int cur, cudaEvent_t* ev, int zb, int ze) {
   if (ev) cudaEventRecord(ev[2], c->stream);
   k_div_sep<T><<<gr, b, 0, c->stream>>>(g, P, tz, c->prm.use_Q, zb, ze);
   if (ev) cudaEventRecord(ev[3], c->stream);
-  {
+  if (fused) {
+    int ftz = std::min(c->sched_ftz, ze - zb);
+    void* args[] = {(void*)&g, (void*)&P, (void*)&ph, (void*)&ftz, (void*)&zb, (void*)&ze};
+    cudaLaunchKernel(fused_kernel(c), fused_grid(c, ze - zb, ftz), dim3(FNT, 1, 1), args, 0, c->stream);
+    c->mac_ready = c->steps + 1;
+  } else {
     void* args[] = {(void*)&g, (void*)&P, (void*)&ph, (void*)&zb};
     cudaLaunchKernel(collide_kernel<T, SF, SOLID>(sm, c->unit), gc, bc, args, 0, c->stream);
+    c->mac_ready = -1;
   }
   if (ev) cudaEventRecord(ev[4], c->stream);
 }
@@ -266,6 +330,11 @@ void launch_passes(cg_ctx* c, int cur, cudaEvent_t* ev, int zb, int ze) {
 // from slabs i+-1, and the overwrites of mac, phi, force and the recoloring
 // state that step t still reads), so the start of a step overlaps the end of
 // the previous one.  Results do not depend on the slabs or the chaining.
+// The fused form has three passes per slab: fields(i) after fused(t-1,
+// i-1..i+1) (it writes mac and phi of step t), div(i) after fields(i-1..i+1),
+// fused(i) after div(i-1..i+1) (its ring planes read F and Q of the slabs
+// beside it); the same edges cover the cross-step hazards, and the graph
+// assumes that the step before it left its sums (mac_ready).
 template <typename T, typename SF, bool SOLID>
 cudaGraphExec_t build_slab_graph(cg_ctx* c, int cur0, int nsteps) {
   const int slab = c->sched_planes;
@@ -304,10 +373,13 @@ cudaGraphExec_t build_slab_graph(cg_ctx* c, int cur0, int nsteps) {
       ok = false;
   };
   std::vector<cudaGraphNode_t> dv;
+  const bool fused = fused_now<T, SF, SOLID>(c);
+  std::vector<int> ftz(ns);
+  for (int i = 0; i < ns; ++i) ftz[i] = std::min(c->sched_ftz, ze[i] - zb[i]);
   for (int s = 0; s < nsteps && ok; ++s) {
     const Ptrs<T>& Pc = P[(cur0 + s) & 1];
     const int sm = next_mode(c->L.inplace, cur0 + s);
-    for (int i = 0; i < ns; ++i) {
+    for (int i = 0; i < ns && !fused; ++i) {
       const dim3 gr((c->prm.nx + TX - 1) / TX, (c->prm.ny + TY - 1) / TY, (ze[i] - zb[i] + tzs[i] - 1) / tzs[i]);
       void* args[] = {(void*)&g, (void*)&Pc, (void*)&ph, (void*)&tzs[i], (void*)&zb[i], (void*)&ze[i]};
       if (s > 0) deps3(Cprev, i, dv); else dv.clear();
@@ -319,7 +391,9 @@ cudaGraphExec_t build_slab_graph(cg_ctx* c, int cur0, int nsteps) {
       void* fn;
       if constexpr (!SOLID && sizeof(T) == 4) fn = (void*)k_fields_sep<T>;
       else fn = (void*)k_fields<T, SOLID>;
-      deps3(M, i, dv);
+      if (!fused) deps3(M, i, dv);
+      else if (s > 0) deps3(Cprev, i, dv);
+      else dv.clear();
       add(&F[i], fn, gr, b, args, dv);
     }
     for (int i = 0; i < ns; ++i) {
@@ -329,6 +403,12 @@ cudaGraphExec_t build_slab_graph(cg_ctx* c, int cur0, int nsteps) {
       add(&D[i], (void*)k_div_sep<T>, gr, b, args, dv);
     }
     for (int i = 0; i < ns; ++i) {
+      if (fused) {
+        void* args[] = {(void*)&g, (void*)&Pc, (void*)&ph, (void*)&ftz[i], (void*)&zb[i], (void*)&ze[i]};
+        deps3(D, i, dv);
+        add(&C[i], fused_kernel(c), fused_grid(c, ze[i] - zb[i], ftz[i]), dim3(FNT, 1, 1), args, dv);
+        continue;
+      }
       const dim3 gc((c->prm.nx + bc.x - 1) / bc.x, (c->prm.ny + bc.y - 1) / bc.y, ze[i] - zb[i]);
       void* args[] = {(void*)&g, (void*)&Pc, (void*)&ph, (void*)&zb[i]};
       dv.assign(1, D[i]);
@@ -366,10 +446,10 @@ bool launch_chain_tuned(cg_ctx* c, cudaGraphExec_t gx) {
   c->sched_cand.erase(c->sched_cand.begin());
   c->tune_phase = 0;
   if (!c->sched_cand.empty()) {
-    set_schedule(c, c->sched_cand.front().first, c->sched_cand.front().second);
+    set_schedule(c, c->sched_cand.front());
   } else {
     const auto best = std::min_element(c->sched_timed.begin(), c->sched_timed.end());
-    set_schedule(c, best->second.first, best->second.second);
+    set_schedule(c, best->second);
   }
   return true;
 }
@@ -396,7 +476,13 @@ int enqueue_steps(cg_ctx* c, int64_t remaining) {
       // a single step inside a timed window would falsify it: time again
       if (!k && !c->sched_cand.empty() && c->tune_phase > 1) c->tune_phase = 1;
       cudaGraphExec_t gx = c->sgraph[k][cur];
-      if (gx && (k ? launch_chain_tuned(c, gx) : cudaGraphLaunch(gx, c->stream) == cudaSuccess)) return n;
+      const bool fused = fused_now<T, SF, SOLID>(c);
+      // the fused graphs start from the sums that the step before left
+      if (gx && fused && c->mac_ready != c->steps) launch_macro<T, SF, SOLID>(c, cur);
+      if (gx && (k ? launch_chain_tuned(c, gx) : cudaGraphLaunch(gx, c->stream) == cudaSuccess)) {
+        c->mac_ready = fused ? c->steps + n : -1;
+        return n;
+      }
       (void)cudaGetLastError();
       c->graphs_ok = false;  // graphs unavailable here: plain launches from now on
     }
@@ -520,6 +606,7 @@ void enqueue_init(cg_ctx* c, const double* d_in, long long lo, long long hi) {
     Ptrs<T> W = make_ptrs<T>(c, 0);
     W.f_out = const_cast<void*>(W.f_in);
     W.aux_out = const_cast<T*>(W.aux_in);
+    W.mac = P.mac;
     k_init_walls<T, SF><<<gr, b, 0, c->stream>>>(g, W, make_phys<T>(c->prm), next_mode(c->L.inplace, 0),
                                                  last_mode(c->L.inplace, 0));
   }
@@ -679,6 +766,7 @@ int cg_init_fields(cg_ctx* c, const double* rho_r, const double* rho_b, const do
   if (bad >= 0)
     return fail(CG_ERR_INVALID_ARG, "densities must be finite and >= 0 (cell " + std::to_string(bad) + ")");
   c->steps = 0;  // the state goes to buffer 0, the staging to buffer 1
+  c->mac_ready = -1;
   const Stage st = stage_of(c);
   double* d_in = reinterpret_cast<double*>(st.p);
   const Geom g = make_geom(c);
@@ -755,19 +843,18 @@ int cg_read_macros(cg_ctx* c, double* rho_r, double* rho_b, double* u, double* p
   double* d_out = reinterpret_cast<double*>(st.p);
   const Geom g = make_geom(c);
   const dim3 b = block_of(c->prm), gr = grid_of(c->prm, b);
-  const int cur = (int)(c->steps & 1);
   // chunks of cells, the seven fields of each chunk staged together
   const long long chunk = chunk_cells(st, 7 * sizeof(double));
   for (long long lo = 0; lo < n; lo += chunk) {
     const long long hi = std::min(n, lo + chunk), m = hi - lo;
     if (c->prm.precision == CG_F64) {
-      auto P = make_ptrs<double>(c, cur);
+      auto P = state_ptrs<double>(c);
       if (c->L.solid)
         k_read_macros<double, true><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), d_out, lo, hi);
       else
         k_read_macros<double, false><<<gr, b, 0, c->stream>>>(g, P, make_phys<double>(c->prm), d_out, lo, hi);
     } else {
-      auto P = make_ptrs<float>(c, cur);
+      auto P = state_ptrs<float>(c);
       if (c->L.solid)
         k_read_macros<float, true><<<gr, b, 0, c->stream>>>(g, P, make_phys<float>(c->prm), d_out, lo, hi);
       else
@@ -848,10 +935,10 @@ int cg_reduce(cg_ctx* c, double out_mass[2], int32_t* nonfinite) {
   double* result = reinterpret_cast<double*>(c->ws + c->L.result);
   if (c->prm.precision == CG_F64)
     k_mass_partial<double><<<c->L.red_blocks, RED_THREADS, 0, c->stream>>>(
-        g, reinterpret_cast<const double*>(c->ws + c->L.mac), c->L.n, partial);
+        g, reinterpret_cast<const double*>(c->ws + mac_last(c)), c->L.n, partial);
   else
     k_mass_partial<float><<<c->L.red_blocks, RED_THREADS, 0, c->stream>>>(
-        g, reinterpret_cast<const float*>(c->ws + c->L.mac), c->L.n, partial);
+        g, reinterpret_cast<const float*>(c->ws + mac_last(c)), c->L.n, partial);
   k_mass_final<<<1, RED_THREADS, 0, c->stream>>>(partial, c->L.red_blocks, result);
   CG_CUDA(cudaGetLastError());
   double m[2];
@@ -898,32 +985,44 @@ int cg_profile_read(cg_ctx* c, double ms[CG_NUM_PASSES], int64_t* steps) {
   return CG_OK;
 }
 
-int cg_set_schedule(cg_ctx* c, int32_t planes, int32_t tz) {
+int cg_set_schedule_form(cg_ctx* c, int32_t planes, int32_t tz, int32_t fused_tz) {
   if (!c) return fail(CG_ERR_INVALID_ARG, "ctx is NULL");
   if (c->batch) return fail(CG_ERR_INVALID_ARG, "the domain is a member of a batch: remove it first");
-  if (planes == 0 && tz == 0) {
+  if (planes == 0 && tz == 0 && fused_tz == 0) {
     CG_CUDA(cudaStreamSynchronize(c->stream));  // graphs of the old schedule may be in flight
     c->sched_planes = 0;  // tune again at the next graph step
+    c->sched_ftz = 0;
     drop_graphs(c);
     return CG_OK;
   }
-  if (planes < 1 || planes > c->prm.nz || tz < 1 || tz > planes)
-    return fail(CG_ERR_INVALID_ARG, "need 1 <= planes <= nz and 1 <= tz <= planes (or both 0)");
+  if (planes < 1 || planes > c->prm.nz || tz < 1 || tz > planes || fused_tz < 0 || fused_tz > planes)
+    return fail(CG_ERR_INVALID_ARG,
+                "need 1 <= planes <= nz, 1 <= tz <= planes and 0 <= fused_tz <= planes (or all 0)");
+  if (fused_tz > 0 && !c->L.fusable)
+    return fail(CG_ERR_UNSUPPORTED, "the fused collision pass needs FP32, two buffers, no walls and a D3Q27 "
+                                    "domain with 8 * stride + nx * ny < 2^31");
   CG_CUDA(cudaStreamSynchronize(c->stream));  // graphs of the old schedule may be in flight
   c->sched_cand.clear();
   c->sched_timed.clear();
-  set_schedule(c, planes, tz);
+  set_schedule(c, StepSched{planes, tz, fused_tz});
   return CG_OK;
 }
 
-int cg_schedule(cg_ctx* c, int32_t* planes, int32_t* tz, int32_t* tuning) {
+int cg_set_schedule(cg_ctx* c, int32_t planes, int32_t tz) { return cg_set_schedule_form(c, planes, tz, 0); }
+
+int cg_schedule_form(cg_ctx* c, int32_t* planes, int32_t* tz, int32_t* fused_tz, int32_t* tuning) {
   if (!c) return fail(CG_ERR_INVALID_ARG, "ctx is NULL");
   if (planes) *planes = c->sched_planes;
   if (tz) *tz = c->sched_tz;
+  if (fused_tz) *fused_tz = c->sched_ftz;
   if (tuning)
     *tuning = c->graphs_ok && c->prm.lattice == CG_D3Q27 &&
               ((c->sched_planes == 0 && c->prm.nz >= SLAB_MIN_NZ) || !c->sched_cand.empty());
   return CG_OK;
+}
+
+int cg_schedule(cg_ctx* c, int32_t* planes, int32_t* tz, int32_t* tuning) {
+  return cg_schedule_form(c, planes, tz, nullptr, tuning);
 }
 
 int cg_steps_taken(cg_ctx* c, int64_t* steps) {
@@ -950,7 +1049,7 @@ int state_regions(const cg_ctx* c, size_t off[6], size_t len[6]) {
   int k = 0;
   off[k] = L.f[cur]; len[k++] = L.nq * (size_t)L.stride * L.pop_elem;
   off[k] = L.s[cur]; len[k++] = L.ns * field;
-  off[k] = L.mac; len[k++] = 5 * field;
+  off[k] = mac_last(c); len[k++] = 5 * field;
   off[k] = L.force; len[k++] = 3 * field;
   if (L.solid) {
     off[k] = L.aux[cur]; len[k++] = L.nq * field;
@@ -1012,6 +1111,7 @@ int cg_load_state(cg_ctx* c, const void* host, size_t bytes) {
       h.solid != (int)c->L.solid || h.lattice != c->prm.lattice || h.streaming != c->prm.streaming)
     return fail(CG_ERR_INVALID_ARG, "checkpoint does not match the domain parameters");
   c->steps = h.steps;  // selects the buffer the regions go to
+  c->mac_ready = -1;
   size_t off[6], len[6];
   int k = state_regions(c, off, len);
   size_t need = sizeof(h);

@@ -80,7 +80,8 @@ struct Ptrs {
   const T* aux_in;
   T* aux_out;
   const uint32_t* mask;
-  T* mac;
+  T* mac;      // rho_r, rho_b, j of the step (written by its macroscopic pass)
+  T* mac_out;  // of the next step (written by the fused collision pass)
   T* phi;
   T* qc;  // correction term Q
   T* force;

@@ -228,7 +228,7 @@ __global__ void k_diag_final2(const double* partial, int nblocks, double* res) {
 template <typename T, bool SOLID>
 void enqueue_diag(cg_ctx* c, const DiagArgs& a, double* partial, double* res) {
   const Geom g = make_geom(c);
-  const Ptrs<T> P = make_ptrs<T>(c, (int)(c->steps & 1));
+  const Ptrs<T> P = state_ptrs<T>(c);
   const int nb = c->L.red_blocks;
   k_diag_partial<T, SOLID><<<nb, DG_THREADS, 0, c->stream>>>(g, P, make_phys<T>(c->prm), a, c->L.n, partial);
   k_diag_final1<<<1, 64, 0, c->stream>>>(partial, nb, g, a, res);

@@ -29,6 +29,17 @@ inline int fail(int code, const std::string& msg) {
 constexpr size_t ALIGN = 256;
 inline size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
+// a schedule of the step graphs: slabs of `planes` planes, tiles of `tz`
+// planes, and the step form (ftz = 0: four passes; > 0: fused collision
+// pass with tiles of ftz planes)
+struct StepSched {
+  int planes = 0, tz = 0, ftz = 0;
+  bool operator==(const StepSched& o) const { return planes == o.planes && tz == o.tz && ftz == o.ftz; }
+  bool operator<(const StepSched& o) const {
+    return planes != o.planes ? planes < o.planes : (tz != o.tz ? tz < o.tz : ftz < o.ftz);
+  }
+};
+
 struct Layout {
   long long n = 0, stride = 0;
   size_t elem = 0;      // bytes of an arithmetic value (FP64 or FP32)
@@ -39,7 +50,12 @@ struct Layout {
   bool inplace = false;  // one population buffer (f[1] == f[0]), updated in place
   int red_blocks = 0;
   size_t f[2] = {0, 0}, s[2] = {0, 0}, aux[2] = {0, 0};
-  size_t mask = 0, mac = 0, phi = 0, qc = 0, force = 0, wv = 0;
+  size_t mask = 0, phi = 0, qc = 0, force = 0, wv = 0;
+  // rho_r, rho_b, j: mac[p] is written by the macroscopic pass of a step of
+  // parity p, or by the fused collision pass of the step before it; the two
+  // are one buffer unless the domain can take the fused pass (fusable)
+  size_t mac[2] = {0, 0};
+  bool fusable = false;
   size_t partial = 0, flag = 0, result = 0, diag = 0, total = 0;
 };
 
@@ -74,9 +90,15 @@ struct cg_ctx {
   // schedule of the graphs: slabs of sched_planes planes, tiles of sched_tz
   // planes (0: not chosen yet); candidates still to time and the timings
   int sched_planes = 0, sched_tz = 0;
-  std::vector<std::pair<int, int>> sched_cand;
-  std::vector<std::pair<float, std::pair<int, int>>> sched_timed;
+  std::vector<cg27::StepSched> sched_cand;
+  std::vector<std::pair<float, cg27::StepSched>> sched_timed;
   int tune_phase = 0;  // 0: next chain untimed, 1..: timed chains of the candidate
+  // the schedule's step form: sched_ftz = 0 runs the four passes, > 0 the
+  // macroscopic pass folded into the collision of the previous step
+  // (k_collide_macro, tiles of sched_ftz planes); mac_ready is the step
+  // whose sums that pass has left in mac[step & 1] (-1: none)
+  int sched_ftz = 0;
+  int64_t mac_ready = -1;
   cudaEvent_t tev[2] = {nullptr, nullptr};
   ~cg_ctx() {
     for (cudaEvent_t e : events) cudaEventDestroy(e);
@@ -132,6 +154,7 @@ inline Geom make_geom(const cg_ctx* c) {
 }
 
 // pointers for a step that reads buffer `cur` and writes buffer 1 - cur
+// (mac: the sums of that step; mac_out: of the next one)
 template <typename T>
 inline Ptrs<T> make_ptrs(const cg_ctx* c, int cur) {
   const Layout& L = c->L;
@@ -144,12 +167,25 @@ inline Ptrs<T> make_ptrs(const cg_ctx* c, int cur) {
   P.aux_in = L.solid ? reinterpret_cast<const T*>(w + L.aux[cur]) : nullptr;
   P.aux_out = L.solid ? reinterpret_cast<T*>(w + L.aux[1 - cur]) : nullptr;
   P.mask = L.solid ? reinterpret_cast<const uint32_t*>(w + L.mask) : nullptr;
-  P.mac = reinterpret_cast<T*>(w + L.mac);
+  P.mac = reinterpret_cast<T*>(w + L.mac[cur]);
+  P.mac_out = reinterpret_cast<T*>(w + L.mac[1 - cur]);
   P.phi = reinterpret_cast<T*>(w + L.phi);
   P.qc = reinterpret_cast<T*>(w + L.qc);
   P.force = reinterpret_cast<T*>(w + L.force);
   P.wv = reinterpret_cast<T*>(w + L.wv);
   P.flag = reinterpret_cast<unsigned int*>(w + L.flag);
+  return P;
+}
+
+// the sums of the last step taken (of the initial state before the first):
+// what the read-back, reductions and checkpoints see
+inline size_t mac_last(const cg_ctx* c) { return c->L.mac[1 - (int)(c->steps & 1)]; }
+
+// pointers of the current state, mac pointing at the last step's sums
+template <typename T>
+inline Ptrs<T> state_ptrs(const cg_ctx* c) {
+  Ptrs<T> P = make_ptrs<T>(c, (int)(c->steps & 1));
+  P.mac = P.mac_out;
   return P;
 }
 

@@ -132,6 +132,35 @@ __device__ __forceinline__ V sub2(V a, V b) {
 template <typename T>
 __device__ __forceinline__ Pr<T> splat(T v) { return pr(v, v); }
 
+// ---- the pulled sums of a cell ---------------------------------------------------------
+// Order in which the 27 pulled terms of a cell's colour and momentum sums are
+// added: the directions with c_z = +1 (source cells in the plane below), then
+// c_z = 0, then c_z = -1, each group in storage order.  A pass that builds the
+// sums source plane by source plane receives the terms in this order, so every
+// kernel that forms them rounds alike.
+__host__ __device__ constexpr int sum_dir(int k) { return 9 * (2 - k / 9) + k % 9; }
+
+template <typename T>
+__device__ __forceinline__ T fma_rn(T a, T b, T c);
+template <>
+__device__ __forceinline__ float fma_rn<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <>
+__device__ __forceinline__ double fma_rn<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// sums m = (rho_r, rho_b, j_x, j_y, j_z) += the term of direction q: the total
+// f pulled from a fluid source whose colour fractions are (wr, wb)
+template <typename T>
+__device__ __forceinline__ void add_pulled(int q, T f, T wr, T wb, T (&m)[5]) {
+  m[0] = fma_rn(wr, f, m[0]);
+  m[1] = fma_rn(wb, f, m[1]);
+  if (CX(q) > 0) m[2] += f;
+  if (CX(q) < 0) m[2] -= f;
+  if (CY(q) > 0) m[3] += f;
+  if (CY(q) < 0) m[3] -= f;
+  if (CZ(q) > 0) m[4] += f;
+  if (CZ(q) < 0) m[4] -= f;
+}
+
 // ---- pass 1 -----------------------------------------------------------------------------
 
 // OFF32 (two buffers only, and 8 stride + nx ny < 2^31): each pulled load is
@@ -217,33 +246,31 @@ __device__ __forceinline__ void macro_tile(const Geom& g, const Ptrs<T>& P, cons
       const T s_rest0 = SHIFT ? ld(P.s_in + S_REST * S + i0) : T(0);
       // sum over q of (w_q / c_s^2) c_q . R(x - c_q), from the divergence pass
       const T divr = ld(P.s_in + S_DIVR * S + i0);
-      T rr = divr, rb = -divr, jx = T(0), jy = T(0), jz = T(0);
+      T m[5] = {divr, -divr, T(0), T(0), T(0)};  // rho_r, rho_b, j
 #pragma unroll
-      for (int q = 0; q < 27; ++q) {
+      for (int k = 0; k < 27; ++k) {
+        const int q = sum_dir(k);
         const int src = c.xs[1 - CX(q)] + c.ys[1 - CY(q)] + zo[1 - CZ(q)];
         const int rq = (z - CZ(q) + RING) & (RING - 1), iq = (c.tx + 1 - CX(q)) + W * (c.ty + 1 - CY(q));
         const V s = PAIRS ? reinterpret_cast<const V*>(sRaw)[rq * PL + iq] : pr(slot(rq, 0, iq), slot(rq, 1, iq));
         if (SHIFT) f[q] = pop_decode<true>(q, f[q], s_rest0, ph.rest1);
-        T ft = f[q];
         if (SOLID && ((mask >> OPP(q)) & 1u)) {
+          // from a wall cell: its red part sits in f, its blue part in aux
           const T fb = ld(P.aux_in + rd_dir<SM>(q) * S + (SM == SM_EVEN ? i0 : src));
-          rr += f[q];
-          rb += fb;
-          ft = f[q] + fb;
+          const T ft = f[q] + fb;
+          m[0] += f[q];
+          m[1] += fb;
+          if (CX(q) != 0) m[2] += T(CX(q)) * ft;
+          if (CY(q) != 0) m[3] += T(CY(q)) * ft;
+          if (CZ(q) != 0) m[4] += T(CZ(q)) * ft;
         } else {
-          rr += s.x * f[q];
-          rb += s.y * f[q];
+          add_pulled(q, f[q], s.x, s.y, m);
         }
-        if (CX(q) != 0) jx += T(CX(q)) * ft;
-        if (CY(q) != 0) jy += T(CY(q)) * ft;
-        if (CZ(q) != 0) jz += T(CZ(q)) * ft;
       }
+      const T rr = m[0], rb = m[1];
       T* const mac = P.mac + i0;  // fields S apart
-      mac[0] = rr;
-      mac[S] = rb;
-      mac[2 * S] = jx;
-      mac[3 * S] = jy;
-      mac[4 * S] = jz;
+#pragma unroll
+      for (int a = 0; a < 5; ++a) mac[a * S] = m[a];
       const bool self_solid = SOLID && ((mask >> SELF_SOLID_BIT) & 1u);
       P.phi[i0] = self_solid ? T(0) : order_parameter(rr, rb, ph);
       if (!isfinite(rr + rb)) atomicOr(P.flag, 1u);
@@ -801,6 +828,33 @@ __device__ __forceinline__ long long pop_index(int q, long long S, int i) {
 // (six 128-thread blocks per SM) so that enough warps keep loads in flight; at
 // this occupancy the kernel streams at about the copy bandwidth of the device.
 
+// The collision of a fluid cell: f holds the 27 pulled totals and becomes
+// f^*; rr, rb are the colour densities of the cell, F the force and Q the
+// correction term of the step.  nu(phi) and tau = 1/2 + rho nu / p
+// (Sec. II.A, the relation of mu and tau), u with half the force (Sec. II.B),
+// then the CM-MRT relaxation of Sec. III.E.
+template <typename T, bool UNIT>
+__device__ __forceinline__ void collide_pulled(T (&f)[27], T rr, T rb, const T (&F)[3], const T (&Q)[3],
+                                               const Phys<T>& ph) {
+  const T rho = rr + rb;
+  const T p = rr * ph.cr2 + rb * ph.cb2;
+  const T phi = order_parameter(rr, rb, ph);
+  const T nu = T(0.5) * (T(1) + phi) * ph.nu_r + T(0.5) * (T(1) - phi) * ph.nu_b;
+  // omega_1 = 1/tau with tau = 1/2 + rho nu / p (Eq. mu = (tau - 1/2) p)
+  const T om1 = p / (T(0.5) * p + rho * nu);
+  T j[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int q = 0; q < 27; ++q)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (CA(q, a) != 0) j[a] += T(CA(q, a)) * f[q];
+  const T inv_rho = T(1) / rho;
+  T u[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u[a] = (j[a] + T(0.5) * F[a]) * inv_rho;
+  collide_cm<T, UNIT>(f, rho, p, u[0], u[1], u[2], F, Q, om1, ph);
+}
+
 template <typename T, typename SF, bool SOLID, bool UNIT, int SM = SM_AB>
 __device__ __forceinline__ void collide_cell(const Geom& g, const Ptrs<T>& P, const Phys<T>& ph, const Cell& c) {
   constexpr int RS = rd_sign<SM>();
@@ -870,23 +924,7 @@ __device__ __forceinline__ void collide_cell(const Geom& g, const Ptrs<T>& P, co
     Q[1] = ld(P.qc + S + i0);
     Q[2] = ld(P.qc + 2 * S + i0);
   }
-  const T rho = rr + rb;
-  const T p = rr * ph.cr2 + rb * ph.cb2;
-  const T phi = order_parameter(rr, rb, ph);
-  const T nu = T(0.5) * (T(1) + phi) * ph.nu_r + T(0.5) * (T(1) - phi) * ph.nu_b;
-  // omega_1 = 1/tau with tau = 1/2 + rho nu / p (Eq. mu = (tau - 1/2) p)
-  const T om1 = p / (T(0.5) * p + rho * nu);
-  T j[3] = {T(0), T(0), T(0)};
-#pragma unroll
-  for (int q = 0; q < 27; ++q)
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-      if (CA(q, a) != 0) j[a] += T(CA(q, a)) * f[q];
-  const T inv_rho = T(1) / rho;
-  T u[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) u[a] = (j[a] + T(0.5) * F[a]) * inv_rho;
-  collide_cm<T, UNIT>(f, rho, p, u[0], u[1], u[2], F, Q, om1, ph);
+  collide_pulled<T, UNIT>(f, rr, rb, F, Q, ph);
   // the rest-direction shift is the value the field pass stored for this cell
   const T r0n = SHIFT ? P.s_out[S_REST * S + i0] : T(0);
   // In place, the slot written for direction q is the slot read for opp q:
@@ -945,6 +983,141 @@ __global__ void __launch_bounds__(128, 6) k_collide(Geom g, Ptrs<T> P, Phys<T> p
   Cell c;
   make_cell_at(g, x, y, zb + blockIdx.z, c);
   collide_cell<T, SF, SOLID, UNIT, SM>(g, P, ph, c);
+}
+
+// ---- fused pass: the collision of a step and the pulled sums of the next ------------------
+// FP32, periodic, two population buffers.  A block owns a TX x TY tile of
+// columns and the planes z0 <= z < z1, and walks the source planes z0-1 .. z1
+// with the tile plus a one-cell ring (FW x FH = 340 positions, one thread
+// each).  Every position pulls the totals of its cell, collides them
+// (collide_pulled) and puts f^* in shared memory; tile cells of the planes
+// z0 .. z1-1 also store f^* to the output buffer.  The tile threads then add
+// the terms of that source plane to the sums of the cells above, at and below
+// it in their column -- the pull of the next step, with the colour fractions
+// of the source cells and DIVR (Eq. (recoloring)) as in the macroscopic pass,
+// in its order (sum_dir) -- and write rho_r, rho_b, j and phi of the next step
+// to mac_out and phi once a cell's third source plane is in.  The ring and the
+// planes z0-1 and z1 belong to other blocks, which collide them with the same
+// instructions, so the f^* summed here are bit for bit the stored ones and the
+// sums equal those of the macroscopic pass on the next step.  The second
+// population read of a step (the macroscopic pass) is gone: per cell the pass
+// moves 152 bytes in and 132 out instead of 248 + 144 for the two passes.
+// Needs 8 stride + nx ny < 2^31 (32-bit offsets of the pulled loads).
+constexpr int FX = 32, FY = 8, FW = FX + 2, FH = FY + 2, FPL = FW * FH, FNT = (FPL + 31) / 32 * 32;
+
+template <bool UNIT>
+__global__ void __launch_bounds__(FNT, 2)
+    k_collide_macro(Geom g, Ptrs<float> P, Phys<float> ph, int tz, int zb, int ze) {
+  using T = float;
+  __shared__ T sF[27][FPL];   // f^* of the source plane
+  __shared__ float2 sW[FPL];  // its colour fractions (rho_r / rho, rho_b / rho)
+  const int z0 = zb + blockIdx.z * tz, z1 = min(ze, z0 + tz);
+  const int tid = threadIdx.x;
+  const long long S = g.stride;
+  // this thread's position: the tile cells, then the ring (the top row, the
+  // bottom row, then both ends of the rows between)
+  const bool has = tid < FPL, tile = tid < FX * FY;
+  int lx = 0, ly = 0;
+  if (tile) {
+    lx = tid % FX + 1;
+    ly = tid / FX + 1;
+  } else if (has) {
+    const int r = tid - FX * FY;
+    if (r < FW) {
+      lx = r;
+    } else if (r < 2 * FW) {
+      lx = r - FW;
+      ly = FH - 1;
+    } else {
+      lx = ((r - 2 * FW) & 1) ? FW - 1 : 0;
+      ly = 1 + (r - 2 * FW) / 2;
+    }
+  }
+  const int pos = lx + FW * ly;
+  const int gx = blockIdx.x * FX + lx - 1, gy = blockIdx.y * FY + ly - 1;
+  const bool own = tile && gx < g.nx && gy < g.ny;
+  const int x = wrapi(gx, g.nx), y = wrapi(gy, g.ny);
+  const int xs[3] = {x == 0 ? g.nx - 1 : x - 1, x, x == g.nx - 1 ? 0 : x + 1};
+  const int ys[3] = {(y == 0 ? g.ny - 1 : y - 1) * g.nx, y * g.nx, (y == g.ny - 1 ? 0 : y + 1) * g.nx};
+  const int cxy = x + y * g.nx;
+  // offset of direction j = (c_x + 1) + 3 (c_y + 1) of a z group from the
+  // group's row base, the source column x - c included
+  int off[9];
+#pragma unroll
+  for (int j = 0; j < 9; ++j) off[j] = j * (int)S + xs[1 - (j % 3 - 1)] + ys[1 - (j / 3 - 1)];
+  const float* const fin = static_cast<const float*>(P.f_in);
+  float* const fout = static_cast<float*>(P.f_out);
+  // the inputs of this thread's cell in a source plane: 27 pulled totals;
+  // rho_r, rho_b, F, Q and the colour fractions
+  T f[27], in[10];
+  auto fetch = [&](int z) {
+    const int zo[3] = {zoff(g, z - 1), zoff(g, z), zoff(g, z + 1)};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float* const base = fin + 9LL * k * S + zo[2 - k];  // group c_z = k - 1 pulls from z - c_z
+#pragma unroll
+      for (int j = 0; j < 9; ++j) f[9 * k + j] = ld(base + off[j]);
+    }
+    const int i = cxy + zo[1];
+    in[0] = ld(P.mac + i);
+    in[1] = ld(P.mac + S + i);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      in[2 + a] = ld(P.force + a * S + i);
+      in[5 + a] = ph.use_Q ? ld(P.qc + a * S + i) : T(0);
+    }
+    in[8] = ld(P.s_out + i);
+    in[9] = ld(P.s_out + S + i);
+  };
+  // sums (rho_r, rho_b, j) of this column's cells in the planes s-1 and s
+  T m_lo[5] = {T(0), T(0), T(0), T(0), T(0)}, m_mid[5] = {T(0), T(0), T(0), T(0), T(0)};
+  if (has) fetch(z0 - 1);
+  for (int s = z0 - 1; s <= z1; ++s) {
+    // the sums of plane s+1 start from its DIVR (Eq. (recoloring) terms)
+    T divr_up = T(0);
+    if (tile && s + 1 < z1) divr_up = ld(P.s_out + S_DIVR * S + cxy + zoff(g, s + 1));
+    if (has) {
+      const T F[3] = {in[2], in[3], in[4]}, Q[3] = {in[5], in[6], in[7]};
+      collide_pulled<T, UNIT>(f, in[0], in[1], F, Q, ph);
+      if (own && s >= z0 && s < z1) {
+        float* const o = fout + (cxy + s * g.nxy);
+#pragma unroll
+        for (int q = 0; q < 27; ++q) o[q * S] = f[q];
+      }
+#pragma unroll
+      for (int q = 0; q < 27; ++q) sF[q][pos] = f[q];
+      sW[pos] = make_float2(in[8], in[9]);
+    }
+    __syncthreads();
+    if (has && s < z1) fetch(s + 1);  // in flight while the sums are formed
+    if (tile) {
+      // fractions of the nine source cells x - c of this plane, j = (c_x + 1) + 3 (c_y + 1)
+      float2 w[9];
+#pragma unroll
+      for (int j = 0; j < 9; ++j) w[j] = sW[pos - (j % 3 - 1) - FW * (j / 3 - 1)];
+      T m_up[5] = {divr_up, -divr_up, T(0), T(0), T(0)};
+      // c_z = +1: plane s+1; c_z = 0: plane s; c_z = -1: plane s-1 (sum_dir order)
+#pragma unroll
+      for (int q = 18; q < 27; ++q) add_pulled(q, sF[q][pos - CX(q) - FW * CY(q)], w[q % 9].x, w[q % 9].y, m_up);
+#pragma unroll
+      for (int q = 9; q < 18; ++q) add_pulled(q, sF[q][pos - CX(q) - FW * CY(q)], w[q % 9].x, w[q % 9].y, m_mid);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) add_pulled(q, sF[q][pos - CX(q) - FW * CY(q)], w[q % 9].x, w[q % 9].y, m_lo);
+      if (own && s - 1 >= z0 && s - 1 < z1) {
+        const int i = cxy + (s - 1) * g.nxy;
+#pragma unroll
+        for (int a = 0; a < 5; ++a) P.mac_out[a * S + i] = m_lo[a];
+        P.phi[i] = order_parameter(m_lo[0], m_lo[1], ph);
+        if (!isfinite(m_lo[0] + m_lo[1])) atomicOr(P.flag, 1u);
+      }
+#pragma unroll
+      for (int a = 0; a < 5; ++a) {
+        m_lo[a] = m_mid[a];
+        m_mid[a] = m_up[a];
+      }
+    }
+    __syncthreads();  // the next plane overwrites sF and sW
+  }
 }
 
 // ---- kernels of a batch of domains -----------------------------------------------------------

@@ -37,7 +37,7 @@ def test_params_struct_layout_matches_header(cg):
     # offsets follow the C declaration order; size includes the trailing ints
     p = cg.cg_params()
     assert ctypes.sizeof(p) == 4 * 6 + 8 * 8 + 8 * 11 + 8 * 3 + 8 + 4 * 6 + 8 * 18 + 4 * 2
-    assert cg.cg_abi_version() == 4
+    assert cg.cg_abi_version() == 5
 
 
 def test_defaults_and_workspace(cg):

@@ -21,6 +21,14 @@ macro(i-1..i+1), div(i) after fields(i-1..i+1), collide(i) after div(i), and
 macro(t+1, i) after collide(t, i-1..i+1).  Every pair of nodes that touch a
 location, one of them writing, must be ordered by a path in the graph, in the
 order of the sequential step (and two slabs of one pass must not conflict).
+
+The fused form (FP32, two buffers) has three passes per slab: fields, div and
+  fused   reads  F pulled and mac[t & 1], FORCE, QC and the fractions of S_out
+                 on the source planes [zb-1, ze] (the tile's planes plus one
+                 recomputed plane on either side), DIVR of S_out on the slab;
+                 writes F, mac[(t+1) & 1] and PHI on the slab
+(fields then reads mac[t & 1]), with the edges fields(t, i) after fused(t-1,
+i-1..i+1), div(i) after fields(i-1..i+1), fused(i) after div(i-1..i+1).
 """
 import itertools
 
@@ -81,6 +89,68 @@ def _accesses(nz, zb, ze, pass_, mode, step):
             rd |= _planes(f, zb, last, nz)
         wr = pw
     return rd, wr
+
+
+def _fused_accesses(nz, zb, ze, pass_, step):
+    s_out = "S%d" % (1 - (step & 1))
+    mac, mac_next = "mac%d" % (step & 1), "mac%d" % (1 - (step & 1))
+    last = ze - 1
+    if pass_ == "fields":
+        rd = _planes("phi", zb - 2, ze + 2, nz) | _planes(mac, zb, ze, nz)
+        wr = set()
+        for f in ("force", "wv", s_out + ".frac", s_out + ".R"):
+            wr |= _planes(f, zb, last, nz)
+    elif pass_ == "div":
+        rd = _planes("wv", zb - 1, ze, nz) | _planes(s_out + ".R", zb - 1, ze, nz)
+        wr = _planes("qc", zb, last, nz) | _planes(s_out + ".divr", zb, last, nz)
+    else:
+        pr, _ = _pop_slots(nz, zb - 1, ze + 1, "two_buffers", step)
+        _, pw = _pop_slots(nz, zb, ze, "two_buffers", step)
+        rd = pr | _planes(s_out + ".divr", zb, last, nz)
+        for f in (mac, "force", "qc", s_out + ".frac"):
+            rd |= _planes(f, zb - 1, ze, nz)
+        wr = pw | _planes(mac_next, zb, last, nz) | _planes("phi", zb, last, nz)
+    return rd, wr
+
+
+def _fused_graph(ns, nsteps, fused_pred=None):
+    pred = {}
+    near = lambda i: {(i + d) % ns for d in (-1, 0, 1)}
+    for t in range(nsteps):
+        for i in range(ns):
+            pred[(t, 0, i)] = {(t - 1, 2, j) for j in near(i)} if t > 0 else set()
+            pred[(t, 1, i)] = {(t, 0, j) for j in near(i)}
+            pred[(t, 2, i)] = {(t, 1, j) for j in (near(i) if fused_pred is None else fused_pred(i))}
+    return pred
+
+
+def _unordered(acc, anc):
+    bad = []
+    for u, v in itertools.combinations(sorted(acc), 2):
+        (ru, wu), (rv, wv) = acc[u], acc[v]
+        if (wu & (rv | wv) or wv & ru) and ((u[0], u[1]) == (v[0], v[1]) or u not in anc[v]):
+            bad.append((u, v))
+    return bad
+
+
+@pytest.mark.parametrize("nz,planes,nsteps", [(128, 16, 3), (32, 16, 4), (48, 16, 3), (40, 16, 3), (72, 24, 3),
+                                              (64, 64, 3)])
+def test_fused_slab_graph_edges_order_every_conflict(nz, planes, nsteps):
+    slabs = _slabs(nz, planes)
+    pred = _fused_graph(len(slabs), nsteps)
+    acc = {(t, p, i): _fused_accesses(nz, *slabs[i], ("fields", "div", "fused")[p], t) for (t, p, i) in pred}
+    assert not _unordered(acc, _ancestors(pred))
+
+
+def test_fused_model_catches_a_missing_edge():
+    """With fused(i) after div(i) alone (the four-pass collision's edge) the
+    ring planes of the fused pass would read Q of the next slab before its
+    divergence pass writes it."""
+    nz, planes = 64, 16
+    slabs = _slabs(nz, planes)
+    pred = _fused_graph(len(slabs), 2, fused_pred=lambda i: {i})
+    acc = {(t, p, i): _fused_accesses(nz, *slabs[i], ("fields", "div", "fused")[p], t) for (t, p, i) in pred}
+    assert _unordered(acc, _ancestors(pred))
 
 
 def _graph(ns, nsteps):

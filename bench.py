@@ -466,14 +466,17 @@ def end_to_end(params, fields, N, K, W, dist):
             "parts_s": {"init_fields": t1 - t0, "steps_and_read_macros": t2 - t1}}
 
 
-def time_mode(wl, fields, prec, streaming, steps):
+def time_mode(wl, fields, prec, streaming, steps, schedule=None):
     """MLUPS of one storage mode and layout (CUDA events around `steps` steps
-    after the graphs are built, best of two) and the workspace it needs."""
+    after the graphs are built, best of two) and the workspace it needs; the
+    tuner's schedule, or `schedule` = (planes, tz, fused_tz) fixed."""
     import torch
     from paper_2309_07801_gb300 import cg
     p = cg.make_params(precision=prec, streaming=streaming, **wl.params())
     d = cg.Domain(p)
     d.init(*fields)
+    if schedule:
+        d.set_schedule(*schedule)
     d.tune()
     d.step(2 * GRAPH_STEPS + 1)
     s = d.stream
@@ -489,8 +492,11 @@ def time_mode(wl, fields, prec, streaming, steps):
     d.close()
     del d
     torch.cuda.empty_cache()
-    return {"MLUPS": wl.cells * steps / (best * 1e-3) / 1e6, "workspace_bytes": cg.cg_workspace_bytes(p),
-            "nonfinite": nonfinite}
+    out = {"MLUPS": wl.cells * steps / (best * 1e-3) / 1e6, "workspace_bytes": cg.cg_workspace_bytes(p),
+           "nonfinite": nonfinite}
+    if schedule:
+        out["schedule"] = list(schedule)
+    return out
 
 
 def variants(wl, fields, value, params, dist):
@@ -505,6 +511,10 @@ def variants(wl, fields, value, params, dist):
     for prec, streaming in (("f32", 1), ("f16s", 1), ("bf16s", 1)):
         head["%s_%s" % (prec, "in_place" if streaming else "two_buffers")] = \
             time_mode(wl, fields, prec, streaming, steps)
+    # the fused step form (collision + next step's pulled sums; chosen
+    # explicitly, the tuner keeps the four passes) on slabs of 64 planes
+    if wl.nz >= 128:
+        head["f32_fused_two_buffers"] = time_mode(wl, fields, "f32", 0, steps, schedule=(64, 32, 64))
     out[wl.name] = head
     if not wl.name.startswith("translating_droplet_128"):
         tw = inputs.translating_droplet(128)
@@ -513,6 +523,7 @@ def variants(wl, fields, value, params, dist):
         for prec, streaming in (("f32", 0), ("f32", 1), ("f16s", 0), ("f16s", 1), ("bf16s", 0), ("bf16s", 1)):
             row["%s_%s" % (prec, "in_place" if streaming else "two_buffers")] = \
                 time_mode(tw, tf, prec, streaming, 800)
+        row["f32_fused_two_buffers"] = time_mode(tw, tf, "f32", 0, 800, schedule=(16, 8, 16))
         out[tw.name] = row
     return out
 

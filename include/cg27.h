@@ -202,9 +202,12 @@ int cg_step(cg_ctx *ctx, int64_t nsteps);
  * macroscopic pass and its second read of the populations leave the step.
  * Its tiles recompute a one-cell ring and one plane above and below (tiles of
  * fused_tz planes); the sums are added in the order of the macroscopic pass,
- * and the results are the same as with the four passes, bit for bit.  The
- * tuner times each candidate above in both forms where the domain can take
- * the fused one.  cg_set_schedule_form(ctx, planes, tz, fused_tz) fixes the
+ * and the results are the same as with the four passes, bit for bit.  Per
+ * cell it moves 392 bytes instead of 500 but repeats the collision on the
+ * recomputed cells, which is issue-bound: on a GB300 the step is slower
+ * (the fused pass takes 9.4 ms per 512^3 step against 8.0 ms for the
+ * collision and the macroscopic pass), so the tuner keeps the four passes
+ * and the form is chosen explicitly.  cg_set_schedule_form(ctx, planes, tz, fused_tz) fixes the
  * schedule and the form (fused_tz = 0: four passes; 1 <= fused_tz <= planes:
  * the fused pass; it also applies to the plain launches of domains below 32
  * planes or under per-pass timing), all 0 starts tuning again;

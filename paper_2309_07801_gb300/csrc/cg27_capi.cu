@@ -171,33 +171,19 @@ constexpr int GRAPH_STEPS = 8;
 // chains of each candidate: one untimed, then TUNE_CHAINS timed
 constexpr int TUNE_CHAINS = 2;
 
-// planes per tile of the fused collision pass over a whole domain: the
-// deepest of 64, 32, 16 that still gives four blocks per SM (two resident,
-// two waves), else 8 -- the pass recomputes two planes per tile
-int fused_depth(const cg_ctx* c, int planes) {
-  const long long tiles = (long long)((c->prm.nx + FX - 1) / FX) * ((c->prm.ny + FY - 1) / FY);
-  int sms = 148;
-  int dev = 0;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  for (int d : {64, 32, 16})
-    if (d <= planes && tiles * ((planes + d - 1) / d) >= 4LL * sms) return d;
-  return std::min(8, planes);
-}
-
 // candidate schedules of a domain with nz >= SLAB_MIN_NZ: thin slabs where the
 // domain holds at least two, and whole-domain kernels with the domain's
-// default depth; each with the four passes and, where the domain can take
-// it, with the fused collision pass (one tile per slab for slabs)
+// default depth, all with the four passes.  (The fused form is not among
+// them: its recomputed ring and planes repeat the issue-bound collision --
+// 1617 instructions per cell against 862 + 425 for the collision and the
+// macroscopic pass -- and it measured 9.4 ms per 512^3 step against 8.0 for
+// the two passes; cg_set_schedule_form still selects it.)
 std::vector<StepSched> schedule_candidates(const cg_ctx* c) {
   std::vector<StepSched> v;
   const int nz = c->prm.nz;
   for (auto pt : {std::make_pair(16, 8), std::make_pair(32, 16), std::make_pair(64, 32)})
-    if (nz >= 2 * pt.first) {
-      v.push_back({pt.first, pt.second, 0});
-      if (c->L.fusable) v.push_back({pt.first, pt.second, pt.first});
-    }
+    if (nz >= 2 * pt.first) v.push_back({pt.first, pt.second, 0});
   v.push_back({nz, std::min(c->tz, nz), 0});
-  if (c->L.fusable) v.push_back({nz, std::min(c->tz, nz), fused_depth(c, nz)});
   return v;
 }
 

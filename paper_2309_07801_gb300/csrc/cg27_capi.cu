@@ -233,6 +233,15 @@ void* collide_kernel(int sm, bool unit) {
   return unit ? (void*)k_collide<T, SF, SOLID, true, SM_AB> : (void*)k_collide<T, SF, SOLID, false, SM_AB>;
 }
 
+// block and grid of a z-marching pass with tiles of shape SH over `planes`
+// planes in tiles of tz planes
+template <class SH>
+dim3 shape_block() { return dim3(SH::TX, SH::TY, 1); }
+template <class SH>
+dim3 shape_grid(const cg_ctx* c, int planes, int tz) {
+  return dim3((c->prm.nx + SH::TX - 1) / SH::TX, (c->prm.ny + SH::TY - 1) / SH::TY, (planes + tz - 1) / tz);
+}
+
 // whether the steps of the domain take the fused collision pass now
 template <typename T, typename SF, bool SOLID>
 bool fused_now(const cg_ctx* c) {
@@ -286,11 +295,13 @@ void launch_passes(cg_ctx* c, int cur, cudaEvent_t* ev, int zb, int ze) {
   }
   if (ev) cudaEventRecord(ev[1], c->stream);
   if constexpr (!SOLID && sizeof(T) == 4)
-    k_fields_sep<T><<<gr, b, 0, c->stream>>>(g, P, ph, tz, zb, ze);
+    k_fields_sep<T><<<shape_grid<FieldShape>(c, ze - zb, tz), shape_block<FieldShape>(), 0, c->stream>>>(
+        g, P, ph, tz, zb, ze);
   else
     k_fields<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph, tz, zb, ze);
   if (ev) cudaEventRecord(ev[2], c->stream);
-  k_div_sep<T><<<gr, b, 0, c->stream>>>(g, P, tz, c->prm.use_Q, zb, ze);
+  k_div_sep<T><<<shape_grid<DivShape>(c, ze - zb, tz), shape_block<DivShape>(), 0, c->stream>>>(
+      g, P, tz, c->prm.use_Q, zb, ze);
   if (ev) cudaEventRecord(ev[3], c->stream);
   if (fused) {
     int ftz = std::min(c->sched_ftz, ze - zb);
@@ -375,18 +386,25 @@ cudaGraphExec_t build_slab_graph(cg_ctx* c, int cur0, int nsteps) {
       const dim3 gr((c->prm.nx + TX - 1) / TX, (c->prm.ny + TY - 1) / TY, (ze[i] - zb[i] + tzs[i] - 1) / tzs[i]);
       void* args[] = {(void*)&g, (void*)&Pc, (void*)&ph, (void*)&tzs[i], (void*)&zb[i], (void*)&ze[i]};
       void* fn;
-      if constexpr (!SOLID && sizeof(T) == 4) fn = (void*)k_fields_sep<T>;
-      else fn = (void*)k_fields<T, SOLID>;
+      dim3 grf = gr, bf = b;
+      if constexpr (!SOLID && sizeof(T) == 4) {
+        fn = (void*)k_fields_sep<T>;
+        grf = shape_grid<FieldShape>(c, ze[i] - zb[i], tzs[i]);
+        bf = shape_block<FieldShape>();
+      } else {
+        fn = (void*)k_fields<T, SOLID>;
+      }
       if (!fused) deps3(M, i, dv);
       else if (s > 0) deps3(Cprev, i, dv);
       else dv.clear();
-      add(&F[i], fn, gr, b, args, dv);
+      add(&F[i], fn, grf, bf, args, dv);
     }
     for (int i = 0; i < ns; ++i) {
       const dim3 gr((c->prm.nx + TX - 1) / TX, (c->prm.ny + TY - 1) / TY, (ze[i] - zb[i] + tzs[i] - 1) / tzs[i]);
       void* args[] = {(void*)&g, (void*)&Pc, (void*)&tzs[i], (void*)&use_Q, (void*)&zb[i], (void*)&ze[i]};
       deps3(F, i, dv);
-      add(&D[i], (void*)k_div_sep<T>, gr, b, args, dv);
+      add(&D[i], (void*)k_div_sep<T>, shape_grid<DivShape>(c, ze[i] - zb[i], tzs[i]), shape_block<DivShape>(),
+          args, dv);
     }
     for (int i = 0; i < ns; ++i) {
       if (fused) {

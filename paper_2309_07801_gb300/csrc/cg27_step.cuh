@@ -36,6 +36,13 @@ struct Shape {
 };
 using ShapeA = Shape<32, 8>;
 using ShapeB = Shape<32, 4>;
+// tile shapes of the single-domain stencil passes (threads 32 x TY; the ring
+// of the tile is recomputed, so taller tiles repeat less of it)
+using FieldShape = Shape<32, 8>;
+using DivShape = Shape<32, 8>;
+// blocks per SM that a register cap aims at: `blocks256` blocks of 256 threads
+template <class SH>
+constexpr int blocks_of(int blocks256) { return blocks256 * 256 / SH::NT > 0 ? blocks256 * 256 / SH::NT : 1; }
 
 __device__ __forceinline__ int wrapi(int v, int n) {
   v %= n;
@@ -964,15 +971,17 @@ __global__ void __launch_bounds__(NT) k_fields(Geom g, Ptrs<T> P, Phys<T> ph, in
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT, 4) k_fields_sep(Geom g, Ptrs<T> P, Phys<T> ph, int tz, int zb, int ze) {
+__global__ void __launch_bounds__(FieldShape::NT, blocks_of<FieldShape>(4))
+    k_fields_sep(Geom g, Ptrs<T> P, Phys<T> ph, int tz, int zb, int ze) {
   const int z0 = zb + blockIdx.z * tz;
-  fields_sep_tile<T>(g, P, ph, z0, min(ze, z0 + tz), blockIdx.x, blockIdx.y);
+  fields_sep_tile<T, FieldShape>(g, P, ph, z0, min(ze, z0 + tz), blockIdx.x, blockIdx.y);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? 4 : 1) k_div_sep(Geom g, Ptrs<T> P, int tz, int use_Q, int zb, int ze) {
+__global__ void __launch_bounds__(DivShape::NT, blocks_of<DivShape>((sizeof(T) == 4) ? 4 : 1))
+    k_div_sep(Geom g, Ptrs<T> P, int tz, int use_Q, int zb, int ze) {
   const int z0 = zb + blockIdx.z * tz;
-  div_sep_tile<T>(g, P, z0, min(ze, z0 + tz), use_Q, blockIdx.x, blockIdx.y);
+  div_sep_tile<T, DivShape>(g, P, z0, min(ze, z0 + tz), use_Q, blockIdx.x, blockIdx.y);
 }
 
 template <typename T, typename SF, bool SOLID, bool UNIT, int SM = SM_AB>

@@ -129,9 +129,10 @@ def recorded_traffic(kernel, cells):
 
 
 def step_slabs(nz, planes=16):
-    """Kernels per pass in one step: the library runs a domain with at least two
-    z slabs of 16 planes as a graph of per-slab kernels (cg27_capi.cu)."""
-    return (nz + planes - 1) // planes if nz >= 2 * planes else 1
+    """Kernels per pass in one step: the library runs a domain of at least 32
+    planes as graphs of per-slab kernels, slabs of `planes` planes (the
+    schedule; planes = nz: one kernel per pass), cg27_capi.cu."""
+    return (nz + planes - 1) // planes if nz >= 32 else 1
 
 
 def make_workload(kind, edge):
@@ -414,7 +415,7 @@ def run_ours(args, dist):
                        "l2": "inputs larger than L2: populations and recoloring state 2 x %.0f MB" %
                              (N * (27 + 6) * 4 / 1e6)},
             "step_roofline": step_roofline, "roofline": roofline,
-            "e2e": e2e, "gpu_launches": len(cg.PASS_NAMES) * K * step_slabs(wl.nz), "clocks": clk,
+            "e2e": e2e, "gpu_launches": len(cg.PASS_NAMES) * K * step_slabs(wl.nz, schedule[0]), "clocks": clk,
             "mass": list(map(float, mass)), "nonfinite": nonfinite}
     single = None
     if not args.no_variants:

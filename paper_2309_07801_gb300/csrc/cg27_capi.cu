@@ -263,13 +263,12 @@ dim3 fused_grid(const cg_ctx* c, int planes, int ftz) {
 template <typename T, typename SF, bool SOLID>
 void launch_macro(cg_ctx* c, int cur) {
   const Geom g = make_geom(c);
-  const dim3 b(TX, TY, 1);
   int zb = 0, ze = c->prm.nz, tz = std::min(c->tz, ze);
-  const dim3 gr((c->prm.nx + TX - 1) / TX, (c->prm.ny + TY - 1) / TY, (ze + tz - 1) / tz);
   const Ptrs<T> P = make_ptrs<T>(c, cur);
   const Phys<T> ph = make_phys<T>(c->prm);
   void* args[] = {(void*)&g, (void*)&P, (void*)&ph, (void*)&tz, (void*)&zb, (void*)&ze};
-  cudaLaunchKernel(macro_kernel<T, SF, SOLID>(c, next_mode(c->L.inplace, cur)), gr, b, args, 0, c->stream);
+  cudaLaunchKernel(macro_kernel<T, SF, SOLID>(c, next_mode(c->L.inplace, cur)), shape_grid<MacroShape>(c, ze, tz),
+                   shape_block<MacroShape>(), args, 0, c->stream);
 }
 
 // One step of the whole domain as plain launches: the four passes, or with
@@ -291,7 +290,8 @@ void launch_passes(cg_ctx* c, int cur, cudaEvent_t* ev, int zb, int ze) {
   if (!fused || c->mac_ready != c->steps) {
     int tz_ = tz;
     void* args[] = {(void*)&g, (void*)&P, (void*)&ph, (void*)&tz_, (void*)&zb, (void*)&ze};
-    cudaLaunchKernel(macro_kernel<T, SF, SOLID>(c, sm), gr, b, args, 0, c->stream);
+    cudaLaunchKernel(macro_kernel<T, SF, SOLID>(c, sm), shape_grid<MacroShape>(c, ze - zb, tz),
+                     shape_block<MacroShape>(), args, 0, c->stream);
   }
   if (ev) cudaEventRecord(ev[1], c->stream);
   if constexpr (!SOLID && sizeof(T) == 4)
@@ -380,7 +380,8 @@ cudaGraphExec_t build_slab_graph(cg_ctx* c, int cur0, int nsteps) {
       const dim3 gr((c->prm.nx + TX - 1) / TX, (c->prm.ny + TY - 1) / TY, (ze[i] - zb[i] + tzs[i] - 1) / tzs[i]);
       void* args[] = {(void*)&g, (void*)&Pc, (void*)&ph, (void*)&tzs[i], (void*)&zb[i], (void*)&ze[i]};
       if (s > 0) deps3(Cprev, i, dv); else dv.clear();
-      add(&M[i], macro_kernel<T, SF, SOLID>(c, sm), gr, b, args, dv);
+      add(&M[i], macro_kernel<T, SF, SOLID>(c, sm), shape_grid<MacroShape>(c, ze[i] - zb[i], tzs[i]),
+          shape_block<MacroShape>(), args, dv);
     }
     for (int i = 0; i < ns; ++i) {
       const dim3 gr((c->prm.nx + TX - 1) / TX, (c->prm.ny + TY - 1) / TY, (ze[i] - zb[i] + tzs[i] - 1) / tzs[i]);

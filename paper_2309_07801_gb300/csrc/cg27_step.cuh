@@ -40,6 +40,7 @@ using ShapeB = Shape<32, 4>;
 // of the tile is recomputed, so taller tiles repeat less of it)
 using FieldShape = Shape<32, 8>;
 using DivShape = Shape<32, 8>;
+using MacroShape = Shape<32, 4>;
 // blocks per SM that a register cap aims at: `blocks256` blocks of 256 threads
 template <class SH>
 constexpr int blocks_of(int blocks256) { return blocks256 * 256 / SH::NT > 0 ? blocks256 * 256 / SH::NT : 1; }
@@ -958,10 +959,10 @@ __device__ __forceinline__ void collide_cell(const Geom& g, const Ptrs<T>& P, co
 // passes; one thread per cell, one z plane per blockIdx.z, for the collision.
 
 template <typename T, typename SF, bool SOLID, int SM = SM_AB, bool OFF32 = false>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !SOLID) ? 4 : 1)
+__global__ void __launch_bounds__(MacroShape::NT, blocks_of<MacroShape>((sizeof(T) == 4 && !SOLID) ? 4 : 1))
     k_macro(Geom g, Ptrs<T> P, Phys<T> ph, int tz, int zb, int ze) {
   const int z0 = zb + blockIdx.z * tz;
-  macro_tile<T, SF, SOLID, SM, ShapeA, true, OFF32>(g, P, ph, z0, min(ze, z0 + tz), blockIdx.x, blockIdx.y);
+  macro_tile<T, SF, SOLID, SM, MacroShape, true, OFF32>(g, P, ph, z0, min(ze, z0 + tz), blockIdx.x, blockIdx.y);
 }
 
 template <typename T, bool SOLID>

@@ -546,7 +546,7 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
   // by (plane - z0) mod 3, a compile-time constant in every unrolled plane
   T ph3[3][K2];
   T n3[3][K1][3];
-  T g3[3][3];
+  T gl3[3];  // |grad phi| at the tile cell (grad phi = |grad phi| n there)
   auto load_phi = [&](int z, auto slot) {
     constexpr int R = decltype(slot)::value;
     const int zo = zoff(g, z);
@@ -591,11 +591,7 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
       n3[R][k][0] = gx * inv_len;
       n3[R][k][1] = gy * inv_len;
       n3[R][k][2] = gz * inv_len;
-      if (k == 0) {
-        g3[R][0] = gx;
-        g3[R][1] = gy;
-        g3[R][2] = gz;
-      }
+      if (k == 0) gl3[R] = g2 * inv_len;
     }
   };
   // (S_z n_b, D_z n_b) of the output plane at the n positions
@@ -641,7 +637,6 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
 #pragma unroll
     for (int f = 0; f < 5; ++f) mac[f] = ld(m + f * S);
   };
-  fetch_mac(z0);
   const int cc = (c.tx + 1) + W1 * (c.ty + 1);  // this thread's tile cell among the n positions
   // one output plane z with slots A = slot of z - 1, B = slot of z, C = slot of z + 1
   auto plane = [&](int z, auto A_, auto B_, auto C_) {
@@ -655,6 +650,7 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
     __syncthreads();
     normals(IC{});                 // n of z+1
     stage_n(IA{}, IB{}, IC{});     // S_z n, D_z n of z from n of z-1, z, z+1
+    fetch_mac(z);                  // in flight during the barrier and the derivatives of n
     __syncthreads();
     if (c.active) {
       const int i0 = c.xs[1] + c.ys[1] + z * g.nxy;
@@ -707,7 +703,7 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
       const T rfac = ph.beta * rr * rb * inv_rho * inv_rho * p;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const T Fa = T(0.5) * ph.sigma * kappa * g3[B][a] + fbody[a];
+        const T Fa = T(0.5) * ph.sigma * kappa * (gl3[B] * nc[a]) + fbody[a];
         const T ua = (mac[2 + a] + T(0.5) * Fa) * inv_rho;
         P.force[a * S + i0] = Fa;
         P.wv[a * S + i0] = (p - rho * Lat<T>::CS2) * ua;
@@ -717,7 +713,6 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
       P.s_out[S + i0] = rb * inv_rho;
       if (ph.shift) P.s_out[S_REST * S + i0] = rest_zero(rho, p);
     }
-    fetch_mac(z + 1);
   };
   // slots (z-1, z, z+1) for z - z0 = 0, 1, 2 mod 3: (2, 0, 1), (0, 1, 2), (1, 2, 0)
   for (int z = z0; z < z1; z += 3) {

@@ -534,6 +534,9 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
   __shared__ V sAB[P2];              // (S_z phi, D_z phi) of the plane whose normals come next
   __shared__ float4 sN4[P1];         // (S_z n_0, D_z n_0, S_z n_1, D_z n_1) of the output plane
   __shared__ V sN2[P1];              // (S_z n_2, D_z n_2)
+  // n of three planes at the ring positions (slots k >= 1), each read only by
+  // the thread that wrote it: kept in shared memory to spare registers
+  __shared__ T sNr[3][K1 - 1][3][SH::NT];
   static_assert(sizeof(T) == 4, "the separable field pass is the FP32 form");
   const Col c = make_col<SH>(g, bx, by);
   const long long S = g.stride;
@@ -545,7 +548,7 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
   // the n positions, grad phi at the tile cell; each a ring of three indexed
   // by (plane - z0) mod 3, a compile-time constant in every unrolled plane
   T ph3[3][K2];
-  T n3[3][K1][3];
+  T n3[3][1][3];  // n of three planes at the tile cell (slot 0)
   T gl3[3];  // |grad phi| at the tile cell (grad phi = |grad phi| n there)
   auto load_phi = [&](int z, auto slot) {
     constexpr int R = decltype(slot)::value;
@@ -588,9 +591,15 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
       }
       const T g2 = gx * gx + gy * gy + gz * gz;
       const T inv_len = g2 > T(1e-24) ? fast_rsqrt(g2) : T(0);
-      n3[R][k][0] = gx * inv_len;
-      n3[R][k][1] = gy * inv_len;
-      n3[R][k][2] = gz * inv_len;
+      if (k == 0) {
+        n3[R][0][0] = gx * inv_len;
+        n3[R][0][1] = gy * inv_len;
+        n3[R][0][2] = gz * inv_len;
+      } else {
+        sNr[R][k - 1][0][c.tid] = gx * inv_len;
+        sNr[R][k - 1][1][c.tid] = gy * inv_len;
+        sNr[R][k - 1][2][c.tid] = gz * inv_len;
+      }
       if (k == 0) gl3[R] = g2 * inv_len;
     }
   };
@@ -603,7 +612,9 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
         T a[3], d[3];
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-          const T lo = n3[L][k][b], mid = n3[M][k][b], hi = n3[U][k][b];
+          const T lo = k == 0 ? n3[L][0][b] : sNr[L][k - 1][b][c.tid];
+          const T mid = k == 0 ? n3[M][0][b] : sNr[M][k - 1][b][c.tid];
+          const T hi = k == 0 ? n3[U][0][b] : sNr[U][k - 1][b][c.tid];
           a[b] = S1 * (lo + hi) + S0 * mid;
           d[b] = T(0.5) * (hi - lo);
         }

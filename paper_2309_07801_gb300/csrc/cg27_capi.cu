@@ -300,7 +300,7 @@ void launch_passes(cg_ctx* c, int cur, cudaEvent_t* ev, int zb, int ze) {
   else
     k_fields<T, SOLID><<<gr, b, 0, c->stream>>>(g, P, ph, tz, zb, ze);
   if (ev) cudaEventRecord(ev[2], c->stream);
-  k_div_sep<T><<<shape_grid<DivShape>(c, ze - zb, tz), shape_block<DivShape>(), 0, c->stream>>>(
+  k_div_sep<T><<<shape_grid<DivShape>(c, ze - zb, tz), dim3(32, DIV_THREADS / 32, 1), 0, c->stream>>>(
       g, P, tz, c->prm.use_Q, zb, ze);
   if (ev) cudaEventRecord(ev[3], c->stream);
   if (fused) {
@@ -404,7 +404,7 @@ cudaGraphExec_t build_slab_graph(cg_ctx* c, int cur0, int nsteps) {
       const dim3 gr((c->prm.nx + TX - 1) / TX, (c->prm.ny + TY - 1) / TY, (ze[i] - zb[i] + tzs[i] - 1) / tzs[i]);
       void* args[] = {(void*)&g, (void*)&Pc, (void*)&tzs[i], (void*)&use_Q, (void*)&zb[i], (void*)&ze[i]};
       deps3(F, i, dv);
-      add(&D[i], (void*)k_div_sep<T>, shape_grid<DivShape>(c, ze[i] - zb[i], tzs[i]), shape_block<DivShape>(),
+      add(&D[i], (void*)k_div_sep<T>, shape_grid<DivShape>(c, ze[i] - zb[i], tzs[i]), dim3(32, DIV_THREADS / 32, 1),
           args, dv);
     }
     for (int i = 0; i < ns; ++i) {

@@ -40,6 +40,11 @@ using ShapeB = Shape<32, 4>;
 // of the tile is recomputed, so taller tiles repeat less of it)
 using FieldShape = Shape<32, 8>;
 using DivShape = Shape<32, 8>;
+// threads of a divergence block: 11 rows of 32 for the 32 x 8 tile, so that
+// each thread loads at most one of the 340 positions of the tile plus halo
+// (rows 8-10 load halo positions only): 40 registers instead of 64 with two
+// positions per thread, four blocks per SM
+constexpr int DIV_THREADS = 352, DIV_BLOCKS = 4;
 using MacroShape = Shape<32, 4>;
 // blocks per SM that a register cap aims at: `blocks256` blocks of 256 threads
 template <class SH>
@@ -85,9 +90,9 @@ __device__ __forceinline__ int ring3(int z) { return (z + 3) % 3; }
 // Positions of a plane's tile-plus-halo region that this thread loads: at most
 // two per thread for the regions used here; `xy` is the wrapped in-plane cell
 // offset (x + nx y) of each, -1 when unused.  Computed once per block.
-template <int HALO, class SH = ShapeA>
+template <int HALO, class SH = ShapeA, int NTB = SH::NT>
 struct HaloSlots {
-  static constexpr int TX = SH::TX, TY = SH::TY, NT = SH::NT;
+  static constexpr int TX = SH::TX, TY = SH::TY, NT = NTB;  // NTB threads (at least the tile's)
   static constexpr int W = TX + 2 * HALO, PL = W * (TY + 2 * HALO);
   static constexpr int K = (PL + NT - 1) / NT;
   int xy[K];
@@ -743,11 +748,11 @@ __device__ __forceinline__ void fields_sep_tile(const Geom& g, const Ptrs<T>& P,
 // positions in registers and stages only their z parts (S_z for the in-plane
 // components, D_z for the z component) of the output plane in shared memory
 // (two buffers, one barrier per plane).
-template <typename T, class SH = ShapeA>
+template <typename T, class SH = ShapeA, int NTB = SH::NT>
 __device__ __forceinline__ void div_sep_tile(const Geom& g, const Ptrs<T>& P, int z0, int z1, int use_Q, int bx,
                                              int by) {
-  constexpr int NT = SH::NT;
-  using HS = HaloSlots<1, SH>;
+  constexpr int NT = NTB;
+  using HS = HaloSlots<1, SH, NTB>;
   constexpr int W = HS::W, PL = HS::PL, K = HS::K;
   constexpr T S0 = T(2) / T(3), S1 = T(1) / T(6);
   __shared__ T sA[2][6][PL];
@@ -791,7 +796,7 @@ __device__ __forceinline__ void div_sep_tile(const Geom& g, const Ptrs<T>& P, in
         }
       }
     __syncthreads();
-    if (c.active) {
+    if (c.active && (NTB == SH::NT || c.ty < SH::TY)) {  // a tile cell
       const int ctr = (c.tx + 1) + W * (c.ty + 1);
       T d[2][3];
 #pragma unroll
@@ -985,10 +990,10 @@ __global__ void __launch_bounds__(FieldShape::NT, blocks_of<FieldShape>(4))
 }
 
 template <typename T>
-__global__ void __launch_bounds__(DivShape::NT, blocks_of<DivShape>((sizeof(T) == 4) ? 4 : 1))
+__global__ void __launch_bounds__(DIV_THREADS, (sizeof(T) == 4) ? DIV_BLOCKS : 1)
     k_div_sep(Geom g, Ptrs<T> P, int tz, int use_Q, int zb, int ze) {
   const int z0 = zb + blockIdx.z * tz;
-  div_sep_tile<T, DivShape>(g, P, z0, min(ze, z0 + tz), use_Q, blockIdx.x, blockIdx.y);
+  div_sep_tile<T, DivShape, DIV_THREADS>(g, P, z0, min(ze, z0 + tz), use_Q, blockIdx.x, blockIdx.y);
 }
 
 template <typename T, typename SF, bool SOLID, bool UNIT, int SM = SM_AB>

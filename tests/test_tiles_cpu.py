@@ -41,11 +41,11 @@ def ring_slots(tx_n, ty_n, h):
     return pos, W, ty_n + 2 * h
 
 
-def halo_slots(tx_n, ty_n, h):
-    """HaloSlots<HALO, Shape<TX, TY>>: position i = tid + k NT of the array."""
+def halo_slots(tx_n, ty_n, h, nt=None):
+    """HaloSlots<HALO, Shape<TX, TY>, NTB>: position i = tid + k NTB of the array."""
     W = tx_n + 2 * h
     PL = W * (ty_n + 2 * h)
-    NT = tx_n * ty_n
+    NT = nt or tx_n * ty_n
     K = (PL + NT - 1) // NT
     return {(tid, k): ((tid + k * NT) % W, (tid + k * NT) // W)
             for tid in range(NT) for k in range(K) if tid + k * NT < PL}, W, ty_n + 2 * h
@@ -70,6 +70,17 @@ def test_ring_slots_cover_the_array_once_with_the_own_cell_first(shape, h):
 def test_halo_slots_cover_the_array_once(shape):
     pos, W, H = halo_slots(*shape, 1)
     _covers_once(pos, W, H)
+
+
+def test_divergence_blocks_of_352_threads():
+    """k_div_sep runs 352 threads on a 32 x 8 tile: one slot per thread covers
+    the 340 positions of tile plus halo once, and the threads that form an
+    output cell (rows below 8) are exactly the tile's 256."""
+    pos, W, H = halo_slots(32, 8, 1, nt=352)
+    _covers_once(pos, W, H)
+    assert max(k for _, k in pos) == 0
+    out = [tid for tid in range(352) if tid // 32 < 8]
+    assert len(out) == 256 and all((tid % 32 + 1, tid // 32 + 1) in set(pos.values()) for tid in out)
 
 
 @pytest.mark.parametrize("shape", SHAPES)

@@ -45,6 +45,9 @@ using DivShape = Shape<32, 8>;
 // (rows 8-10 load halo positions only): 40 registers instead of 64 with two
 // positions per thread, four blocks per SM
 constexpr int DIV_THREADS = 352, DIV_BLOCKS = 4;
+// output rows per computing thread of the divergence pass (the x parts of the
+// stencils of a shared-memory row are formed once for both rows)
+constexpr int DIV_ROWS = 2;
 using MacroShape = Shape<32, 4>;
 // blocks per SM that a register cap aims at: `blocks256` blocks of 256 threads
 template <class SH>
@@ -796,29 +799,43 @@ __device__ __forceinline__ void div_sep_tile(const Geom& g, const Ptrs<T>& P, in
         }
       }
     __syncthreads();
-    if (c.active && (NTB == SH::NT || c.ty < SH::TY)) {  // a tile cell
-      const int ctr = (c.tx + 1) + W * (c.ty + 1);
-      T d[2][3];
+    // ROWS output rows per computing thread: per vector and shared-memory row
+    // the x parts of the three stencils (D_x, and S_x twice) once, then per
+    // output row the y parts; the two vectors one after the other
+    constexpr int ROWS = (SH::TY % DIV_ROWS == 0) ? DIV_ROWS : 1;
+    if (c.ty < SH::TY / ROWS) {
+      const int cx = c.tx + 1, x = c.x0 + c.tx;
 #pragma unroll
-      for (int v = 0; v < 2; ++v) {
+      for (int v = 0; v < 2; ++v) {  // (p - rho c_s^2) u -> Q; R -> DIVR
+        if (v == 0 && !use_Q) continue;
+        T dAx[ROWS + 2], sAy[ROWS + 2], sB[ROWS + 2];
         const T* Ax = A[3 * v];
         const T* Ay = A[3 * v + 1];
         const T* B = A[3 * v + 2];
-        d[v][0] = T(0.5) * (S1 * (Ax[ctr + 1 - W] - Ax[ctr - 1 - W]) + S0 * (Ax[ctr + 1] - Ax[ctr - 1]) +
-                            S1 * (Ax[ctr + 1 + W] - Ax[ctr - 1 + W]));
-        d[v][1] = T(0.5) * (S1 * (Ay[ctr - 1 + W] - Ay[ctr - 1 - W]) + S0 * (Ay[ctr + W] - Ay[ctr - W]) +
-                            S1 * (Ay[ctr + 1 + W] - Ay[ctr + 1 - W]));
-        d[v][2] = S1 * (S1 * B[ctr - 1 - W] + S0 * B[ctr - W] + S1 * B[ctr + 1 - W]) +
-                  S0 * (S1 * B[ctr - 1] + S0 * B[ctr] + S1 * B[ctr + 1]) +
-                  S1 * (S1 * B[ctr - 1 + W] + S0 * B[ctr + W] + S1 * B[ctr + 1 + W]);
+#pragma unroll
+        for (int r = 0; r < ROWS + 2; ++r) {
+          const int o = (ROWS * c.ty + r) * W + cx;
+          dAx[r] = Ax[o + 1] - Ax[o - 1];
+          sAy[r] = S1 * Ay[o - 1] + S0 * Ay[o] + S1 * Ay[o + 1];
+          sB[r] = S1 * B[o - 1] + S0 * B[o] + S1 * B[o + 1];
+        }
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i) {
+          const int y = c.y0 + ROWS * c.ty + i;
+          if (x >= g.nx || y >= g.ny) continue;
+          const T d0 = T(0.5) * (S1 * dAx[i] + S0 * dAx[i + 1] + S1 * dAx[i + 2]);
+          const T d1 = T(0.5) * (sAy[i + 2] - sAy[i]);
+          const T d2 = S1 * sB[i] + S0 * sB[i + 1] + S1 * sB[i + 2];
+          const int i0 = x + y * g.nx + z * g.nxy;
+          if (v == 0) {
+            qc[0][i0] = T(-3) * d0;
+            qc[1][i0] = T(-3) * d1;
+            qc[2][i0] = T(-3) * d2;
+          } else {
+            divr[i0] = -(d0 + d1 + d2);
+          }
+        }
       }
-      const int i0 = c.xs[1] + c.ys[1] + z * g.nxy;
-      if (use_Q) {
-        qc[0][i0] = T(-3) * d[0][0];
-        qc[1][i0] = T(-3) * d[0][1];
-        qc[2][i0] = T(-3) * d[0][2];
-      }
-      divr[i0] = -(d[1][0] + d[1][1] + d[1][2]);
     }
 #pragma unroll
     for (int k = 0; k < K; ++k)
